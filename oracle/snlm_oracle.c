@@ -1,0 +1,362 @@
+/*
+ * FP64 CPU oracle for separable non-local means (Ghosh & Chaudhury,
+ * "Fast Separable Non-Local Means", arXiv:1407.2343).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is used by tests/, by the smoke check
+ * and by the benchmark's CPU-baseline / reference leg. The product path (the
+ * CUDA library under paper_1407_2343_gb300/) never links, imports or calls it,
+ * and it shares no code, header, table or helper with that path.
+ *
+ * What it computes is the plain definition, one pixel at a time, in double
+ * precision, with explicit (2K+1)-tap patch sums: no lifting, no running sums,
+ * no symmetry reuse. Each function names the passage it follows.
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *  - Boundary: half-sample symmetric extension, applied to patch samples and
+ *    to search positions alike, repeated with period 2N when the reach S+K
+ *    exceeds the signal (the paper comments the extension sentence out in
+ *    Sec. II; Alg. 2/3 index f(j) and f(2i-j) outside [1,N]).
+ *  - Gaussian profile: the truncated (2K+1)-tap g_beta on [-K,K] exactly as in
+ *    Eq. (3), not a recursive approximation.
+ *  - Divergence: Eq. (24) taken literally, with every sample read through the
+ *    extension; its patch term runs over the offsets of the search window that
+ *    also satisfy |j-i| <= K (the Appendix sums over the window only).
+ *  - SURE solve: A theta = b with A from Eq. (19) and b from Eq. (25); when A is
+ *    (numerically) singular the minimum-norm pseudo-inverse solution is used.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_BOX 0
+#define ORC_GAUSS 1
+
+#define ORC_RC 0
+#define ORC_CR 1
+#define ORC_AVG 2
+#define ORC_SURE 3
+
+/* Half-sample symmetric extension of an index into [0, N): the extended
+ * signal satisfies fe(-1) = f(0), fe(N) = f(N-1), and is 2N-periodic. */
+int64_t orc_ext(int64_t x, int64_t N)
+{
+    int64_t p = 2 * N;
+    int64_t y = x % p;
+    if (y < 0)
+        y += p;
+    if (y >= N)
+        y = p - 1 - y;
+    return y;
+}
+
+/* Patch profile g_beta(k), k in [-K, K] (Sec. II, after Eq. (3)): the box
+ * profile is 1 everywhere; the Gaussian is exp(-k^2 / (2 beta^2)). */
+void orc_profile(int K, int profile, double beta, double *g)
+{
+    for (int k = -K; k <= K; ++k)
+        g[k + K] = (profile == ORC_GAUSS) ? exp(-((double)k * k) / (2.0 * beta * beta)) : 1.0;
+}
+
+/* Smoothing parameter rule used when the caller gives none:
+ * h = sigma * sqrt(sum_k g(k)), which is sigma*sqrt(2K+1) for the box. */
+double orc_default_h(double sigma, int K, int profile, double beta)
+{
+    double g[2 * 64 + 1];
+    if (K > 64)
+        return -1.0;
+    orc_profile(K, profile, beta, g);
+    double s = 0.0;
+    for (int k = 0; k <= 2 * K; ++k)
+        s += g[k];
+    return sigma * sqrt(s);
+}
+
+/* Copy one line (n samples, element stride `stride`) into the extended signal
+ * fe[0 .. n + 2R), where fe[R + x] = f(ext(x)) for x in [-R, n + R). */
+static void extend_line(const double *f, int64_t n, int64_t stride, int64_t R, double *fe)
+{
+    for (int64_t x = -R; x < n + R; ++x)
+        fe[R + x] = f[orc_ext(x, n) * stride];
+}
+
+/* Eq. (3): squared patch distance between the patches centred at i and j of
+ * the extended signal (fe is indexed with the offset R already added). */
+static double patch_dist2(const double *fe, int64_t i, int64_t j, int K, const double *g)
+{
+    double d = 0.0;
+    for (int k = -K; k <= K; ++k) {
+        double a = fe[i + k] - fe[j + k];
+        d += g[k + K] * a * a;
+    }
+    return d;
+}
+
+/* Patch distances of n_lines signals of length N (row-major, line after line):
+ * out[(line*N + i)*(2S+1) + (s+S)] = d^2(i, i+s) of Eq. (3), s in [-S, S]. */
+int orc_patch_dist_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, int profile,
+                      double beta, double *out, int nthreads)
+{
+    if (N < 1 || S < 0 || K < 0 || K > 64 || n_lines < 0)
+        return -1;
+    double g[2 * 64 + 1];
+    orc_profile(K, profile, beta, g);
+    const int64_t R = (int64_t)S + K;
+    const int64_t L = N + 2 * R;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t ln = 0; ln < n_lines; ++ln) {
+        double *fe = (double *)malloc(sizeof(double) * (size_t)L);
+        extend_line(x + ln * N, N, 1, R, fe);
+        for (int64_t i = 0; i < N; ++i)
+            for (int s = -S; s <= S; ++s)
+                out[(ln * N + i) * (2 * S + 1) + (s + S)] = patch_dist2(fe, R + i, R + i + s, K, g);
+        free(fe);
+    }
+    return 0;
+}
+
+/* One-dimensional NLM of Eq. (4) with the divergence of Eq. (24) (the pair
+ * that Alg. 3 computes), for one line with element strides:
+ *   fhat(i)  = sum_j w_ij f(j) / W_i,   w_ij = exp(-d^2_ij / h^2),  |j-i| <= S
+ *   dout(i)  = din(i) * dfhat(i)/df(i)   (the chaining used by Alg. 4)
+ * with d^2 from Eq. (3). `din` may alias `dout`; either may be NULL together. */
+static void nlm_line(const double *f, int64_t N, int64_t stride, const double *din, double *fhat,
+                     double *dout, int64_t ostride, int S, int K, double h, const double *g,
+                     double *fe /* scratch, N + 2(S+K) */)
+{
+    const int64_t R = (int64_t)S + K;
+    extend_line(f, N, stride, R, fe);
+    const double h2 = h * h;
+    const int KT = K < S ? K : S; /* patch-overlap offsets that lie in the window */
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t ci = R + i;
+        double W = 0.0, P1 = 0.0, P2 = 0.0;
+        for (int s = -S; s <= S; ++s) {
+            double w = exp(-patch_dist2(fe, ci, ci + s, K, g) / h2);
+            double fj = fe[ci + s];
+            W += w;
+            P1 += w * fj;
+            P2 += w * fj * fj;
+        }
+        const double fh = P1 / W;
+        fhat[i * ostride] = fh;
+        if (dout) {
+            /* Last term of Eq. (24): sum over |j - i| <= K of
+             * w_ij g(i-j) (f(j) - fhat(i)) (f(2i-j) - f(i)). */
+            double T = 0.0;
+            for (int s = -KT; s <= KT; ++s) {
+                double w = exp(-patch_dist2(fe, ci, ci + s, K, g) / h2);
+                T += w * g[-s + K] * (fe[ci + s] - fh) * (fe[ci - s] - fe[ci]);
+            }
+            double div = 2.0 / (h2 * W) * P2 + 1.0 / W - 2.0 / h2 * fh * fh + 2.0 / (W * h2) * T;
+            double d0 = din ? din[i * ostride] : 1.0;
+            dout[i * ostride] = d0 * div;
+        }
+    }
+}
+
+/* Eq. (4) (+ Eq. (24)) applied to n_lines contiguous signals of length N.
+ * delta_in may be NULL (taken as ones); delta_out may be NULL (not computed). */
+int orc_nlm_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, double h, int profile,
+               double beta, const double *delta_in, double *fhat, double *delta_out, int nthreads)
+{
+    if (N < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0) || n_lines < 0)
+        return -1;
+    double g[2 * 64 + 1];
+    orc_profile(K, profile, beta, g);
+    const int64_t L = N + 2 * ((int64_t)S + K);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t ln = 0; ln < n_lines; ++ln) {
+        double *fe = (double *)malloc(sizeof(double) * (size_t)L);
+        nlm_line(x + ln * N, N, 1, delta_in ? delta_in + ln * N : NULL, fhat + ln * N,
+                 delta_out ? delta_out + ln * N : NULL, 1, S, K, h, g, fe);
+        free(fe);
+    }
+    return 0;
+}
+
+/* Apply the 1-D map to every row (axis 0) or every column (axis 1) of an H x W
+ * row-major image; the derivative sequence is chained in place (Alg. 4). */
+static void sweep(const double *src, double *dst, double *delta, int64_t H, int64_t W, int axis,
+                  int S, int K, double h, const double *g, int nthreads)
+{
+    const int64_t n_lines = axis == 0 ? H : W;
+    const int64_t N = axis == 0 ? W : H;
+    const int64_t line_step = axis == 0 ? W : 1;
+    const int64_t elem_step = axis == 0 ? 1 : W;
+    const int64_t L = N + 2 * ((int64_t)S + K);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t ln = 0; ln < n_lines; ++ln) {
+        double *fe = (double *)malloc(sizeof(double) * (size_t)L);
+        nlm_line(src + ln * line_step, N, elem_step, delta ? delta + ln * line_step : NULL,
+                 dst + ln * line_step, delta ? delta + ln * line_step : NULL, elem_step, S, K, h, g, fe);
+        free(fe);
+    }
+}
+
+/* Minimum-norm solution of the symmetric 2x2 system [a c; c e] t = b.
+ * Regular case: Cramer's rule. Singular case (det <= 1e-12 * trace^2): the
+ * pseudo-inverse, i.e. the projection on the dominant eigenvector. */
+static void solve2_sym(double a, double c, double e, const double *b, double *t)
+{
+    double det = a * e - c * c;
+    double tr = a + e;
+    if (det > 1e-12 * tr * tr) {
+        t[0] = (e * b[0] - c * b[1]) / det;
+        t[1] = (a * b[1] - c * b[0]) / det;
+        return;
+    }
+    double half = 0.5 * (a - e);
+    double lam = 0.5 * tr + sqrt(half * half + c * c);
+    if (!(lam > 0.0)) {
+        t[0] = t[1] = 0.0;
+        return;
+    }
+    /* eigenvector of the largest eigenvalue */
+    double v0, v1;
+    if (fabs(c) > 0.0) {
+        v0 = c;
+        v1 = lam - a;
+    } else if (a >= e) {
+        v0 = 1.0;
+        v1 = 0.0;
+    } else {
+        v0 = 0.0;
+        v1 = 1.0;
+    }
+    double nv = sqrt(v0 * v0 + v1 * v1);
+    v0 /= nv;
+    v1 /= nv;
+    double coef = (v0 * b[0] + v1 * b[1]) / lam;
+    t[0] = coef * v0;
+    t[1] = coef * v1;
+}
+
+/* Separable NLM, Alg. 4 (Sec. III):
+ *   f_r  = rows(f),  f_rc = cols(f_r)   with delta_1 chained (Eq. (21))
+ *   f_c  = cols(f),  f_cr = rows(f_c)   with delta_2 chained (Eq. (22))
+ *   out  = theta_1 f_rc + theta_2 f_cr  (Eq. (14))
+ * order RC: theta = (1,0); CR: (0,1); AVG: (1/2,1/2); SURE: A theta = b with
+ * A from Eq. (19) and b from Eq. (25).
+ * info (may be NULL) receives 10 doubles:
+ *   theta1, theta2, A11, A12, A22, sum(f f_rc), sum(f f_cr), sum d1, sum d2, sigma^2. */
+int orc_snlm(const double *img, int64_t H, int64_t W, int S, int K, double h, int profile,
+             double beta, int order, double sigma, double *out, double *info, int nthreads)
+{
+    if (H < 1 || W < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0) || order < 0 || order > 3)
+        return -1;
+    if (order == ORC_SURE && !(sigma >= 0.0))
+        return -1;
+    double g[2 * 64 + 1];
+    orc_profile(K, profile, beta, g);
+    const int64_t n = H * W;
+    const int need_rc = order != ORC_CR;
+    const int need_cr = order != ORC_RC;
+    const int need_div = order == ORC_SURE;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *frc = need_rc ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    double *fcr = need_cr ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    double *d1 = need_div ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    double *d2 = need_div ? (double *)malloc(sizeof(double) * (size_t)n) : NULL;
+    if (!tmp || (need_rc && !frc) || (need_cr && !fcr) || (need_div && (!d1 || !d2))) {
+        free(tmp); free(frc); free(fcr); free(d1); free(d2);
+        return -3;
+    }
+    if (need_div)
+        for (int64_t p = 0; p < n; ++p)
+            d1[p] = d2[p] = 1.0;
+    if (need_rc) {
+        sweep(img, tmp, d1, H, W, 0, S, K, h, g, nthreads); /* f_r  */
+        sweep(tmp, frc, d1, H, W, 1, S, K, h, g, nthreads); /* f_rc */
+    }
+    if (need_cr) {
+        sweep(img, tmp, d2, H, W, 1, S, K, h, g, nthreads); /* f_c  */
+        sweep(tmp, fcr, d2, H, W, 0, S, K, h, g, nthreads); /* f_cr */
+    }
+    double th[2] = {0.0, 0.0};
+    double A11 = 0, A12 = 0, A22 = 0, Bf1 = 0, Bf2 = 0, Sd1 = 0, Sd2 = 0;
+    if (order == ORC_RC) {
+        th[0] = 1.0;
+    } else if (order == ORC_CR) {
+        th[1] = 1.0;
+    } else if (order == ORC_AVG) {
+        th[0] = th[1] = 0.5;
+    } else {
+        for (int64_t p = 0; p < n; ++p) {
+            A11 += frc[p] * frc[p];
+            A12 += frc[p] * fcr[p];
+            A22 += fcr[p] * fcr[p];
+            Bf1 += img[p] * frc[p];
+            Bf2 += img[p] * fcr[p];
+            Sd1 += d1[p];
+            Sd2 += d2[p];
+        }
+        double b[2] = {Bf1 - sigma * sigma * Sd1, Bf2 - sigma * sigma * Sd2};
+        solve2_sym(A11, A12, A22, b, th);
+    }
+    for (int64_t p = 0; p < n; ++p) {
+        double v = 0.0;
+        if (need_rc)
+            v += th[0] * frc[p];
+        if (need_cr)
+            v += th[1] * fcr[p];
+        out[p] = v;
+    }
+    if (info) {
+        info[0] = th[0]; info[1] = th[1];
+        info[2] = A11; info[3] = A12; info[4] = A22;
+        info[5] = Bf1; info[6] = Bf2; info[7] = Sd1; info[8] = Sd2;
+        info[9] = sigma * sigma;
+    }
+    free(tmp); free(frc); free(fcr); free(d1); free(d2);
+    return 0;
+}
+
+/* Intermediate images of Alg. 4 for tests: f_r, f_rc, f_c, f_cr and the two
+ * chained derivative maps delta_1, delta_2 (each H*W, any may be NULL). */
+int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double h, int profile,
+                   double beta, double *fr, double *frc, double *fc, double *fcr, double *d1,
+                   double *d2, int nthreads)
+{
+    if (H < 1 || W < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0))
+        return -1;
+    double g[2 * 64 + 1];
+    orc_profile(K, profile, beta, g);
+    const int64_t n = H * W;
+    double *a = (double *)malloc(sizeof(double) * (size_t)n);
+    double *b = (double *)malloc(sizeof(double) * (size_t)n);
+    double *da = (double *)malloc(sizeof(double) * (size_t)n);
+    double *db = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!a || !b || !da || !db) {
+        free(a); free(b); free(da); free(db);
+        return -3;
+    }
+    for (int64_t p = 0; p < n; ++p)
+        da[p] = db[p] = 1.0;
+    sweep(img, a, da, H, W, 0, S, K, h, g, nthreads);
+    if (fr) memcpy(fr, a, sizeof(double) * (size_t)n);
+    sweep(a, b, da, H, W, 1, S, K, h, g, nthreads);
+    if (frc) memcpy(frc, b, sizeof(double) * (size_t)n);
+    if (d1) memcpy(d1, da, sizeof(double) * (size_t)n);
+    sweep(img, a, db, H, W, 1, S, K, h, g, nthreads);
+    if (fc) memcpy(fc, a, sizeof(double) * (size_t)n);
+    sweep(a, b, db, H, W, 0, S, K, h, g, nthreads);
+    if (fcr) memcpy(fcr, b, sizeof(double) * (size_t)n);
+    if (d2) memcpy(d2, db, sizeof(double) * (size_t)n);
+    free(a); free(b); free(da); free(db);
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
