@@ -1,0 +1,150 @@
+/*
+ * snlm.h - C ABI of libsnlm, a GB300 (sm_103a) implementation of the separable
+ * non-local means filter of Ghosh & Chaudhury, "Fast Separable Non-Local Means"
+ * (arXiv:1407.2343).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an snlm_status (0 = success). No exception crosses the
+ *    ABI and nothing aborts the process.
+ *  - Arguments are validated before any work is queued; on an argument error the
+ *    outputs are left untouched.
+ *  - Pointers documented as DEVICE must point to memory of the current CUDA
+ *    device (cudaMalloc, cudaMallocAsync, or any allocator that hands out such
+ *    memory, e.g. a PyTorch CUDA tensor). The caller owns all memory passed in;
+ *    the library never frees it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Device work is queued asynchronously on it; the call returns
+ *    before the work finishes unless stated otherwise.
+ *  - Images are row-major. `pitch` is the distance between consecutive rows in
+ *    ELEMENTS of the input type (pitch >= W).
+ *  - Boundaries use half-sample symmetric extension (f(-1) = f(0),
+ *    f(N) = f(N-1)), repeated with period 2N when S + K >= N; it applies to the
+ *    samples of a patch and to search positions alike.
+ *  - Limits: 0 <= K <= SNLM_MAX_K, 0 <= S <= SNLM_MAX_S, H, W >= 1,
+ *    H * W < 2^31, h > 0 and finite.
+ */
+#ifndef SNLM_H
+#define SNLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNLM_MAX_K 7
+#define SNLM_MAX_S 128
+
+typedef enum {
+    SNLM_OK = 0,
+    SNLM_ERR_ARG = -1,         /* an argument is out of range or a pointer is null */
+    SNLM_ERR_CUDA = -2,        /* a CUDA call failed (launch, copy, or a sticky device error) */
+    SNLM_ERR_NOMEM = -3,       /* device or host memory could not be obtained */
+    SNLM_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    SNLM_ERR_UNSUPPORTED = -5  /* valid request outside the compiled configurations */
+} snlm_status;
+
+typedef enum { SNLM_U8 = 0, SNLM_F16 = 1, SNLM_F32 = 2 } snlm_dtype;
+
+/* Patch profile g_beta (Sec. II, Eq. (3)): box (g = 1) or Gaussian
+ * g(k) = exp(-k^2 / (2 beta^2)), both truncated to k in [-K, K]. */
+typedef enum { SNLM_BOX = 0, SNLM_GAUSS = 1 } snlm_profile;
+
+/* How the row-then-column (RC) and column-then-row (CR) results are combined
+ * (Sec. III, Eq. (14)): RC alone, CR alone, their average, or the SURE-optimal
+ * weights of Sec. III-A (Eqs. (17), (19), (25); Alg. 4). */
+typedef enum { SNLM_RC = 0, SNLM_CR = 1, SNLM_AVG = 2, SNLM_SURE = 3 } snlm_order;
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *snlm_status_str(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int snlm_version(void);
+
+/* Default smoothing parameter h = sigma * sqrt(sum_{k=-K..K} g(k)); for the
+ * box profile this is sigma * sqrt(2K+1). beta <= 0 selects beta = K/2.
+ * Returns -1 on an invalid argument. Host-only; no device work. */
+float snlm_default_h(float sigma, int K, int profile, float beta);
+
+/* Bytes of device scratch that snlm_denoise_ws needs for an H x W image with the
+ * given order. Returns 0 on an invalid argument. Host-only. */
+size_t snlm_workspace_bytes(int H, int W, int order);
+
+/*
+ * Separable NLM of one image: Alg. 4 of the paper without the bilateral
+ * post-filter of Sec. III-B. Each 1-D pass is the NLM of Eq. (4) along rows or
+ * columns, with patch distances of Eq. (3) and weights w = exp(-d^2/h^2).
+ *   img    DEVICE, H rows of `pitch` elements of type `dtype` (u8, f16 or f32).
+ *   out    DEVICE, H*W float32, dense row-major; receives
+ *          RC: f_rc, CR: f_cr, AVG: (f_rc + f_cr)/2,
+ *          SURE: theta1 f_rc + theta2 f_cr with theta solving Eq. (19)/(25).
+ *   S, K   search half-width and patch half-width.
+ *   h      smoothing parameter (> 0); see snlm_default_h.
+ *   profile, beta   patch profile; beta <= 0 selects K/2 (ignored for box).
+ *   order  snlm_order.
+ *   sigma  noise standard deviation, used only by SNLM_SURE (>= 0).
+ * Scratch comes from a per-device pool inside the library (grown on demand with
+ * cudaMalloc, kept until process exit); calls on one device must therefore not
+ * run concurrently from several host threads. Use snlm_denoise_ws to supply
+ * scratch instead.
+ */
+int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                 int profile, int order, float sigma, float beta, float *out, void *stream);
+
+/*
+ * As snlm_denoise, with caller-provided DEVICE scratch of at least
+ * snlm_workspace_bytes(H, W, order) bytes (16-byte aligned), and an optional
+ * DEVICE pointer `info` (NULL allowed) that receives 10 doubles:
+ *   theta1, theta2, A11, A12, A22, sum f*f_rc, sum f*f_cr, sum delta1,
+ *   sum delta2, sigma^2   (A and the sums of Eqs. (19) and (25); theta of Eq. (14)).
+ * The sums are filled only for SNLM_SURE; theta is always filled.
+ */
+int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                    int profile, int order, float sigma, float beta, float *out, void *workspace,
+                    size_t workspace_bytes, double *info, void *stream);
+
+/*
+ * End-to-end variant for HOST buffers: copies `img_host` (H rows of `pitch`
+ * elements) to the device, runs snlm_denoise, and copies the H*W float32 result
+ * into `out_host`, all on `stream`; returns after the result is in `out_host`.
+ * Pinned (page-locked) host memory gives asynchronous copies; pageable memory
+ * works but is slower. Device buffers come from the library's pool.
+ */
+int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, int S, int K,
+                      float h, int profile, int order, float sigma, float beta, float *out_host,
+                      void *stream);
+
+/*
+ * One 1-D NLM pass (Eq. (4)) over n_lines signals, with the derivative chain of
+ * Eq. (24) when delta_out is given (the computation of Alg. 3).
+ *   x          DEVICE, samples of type dtype; sample i of line l is at
+ *              x[l*line_step + i*elem_step] (elements).
+ *   fhat       DEVICE float32, same indexing with (out_line_step, out_elem_step).
+ *   delta_in   DEVICE float32 or NULL (all ones), same indexing as fhat.
+ *   delta_out  DEVICE float32 or NULL (not computed), same indexing as fhat; may
+ *              alias delta_in.
+ * fhat must not overlap x.
+ */
+int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_step,
+                long long elem_step, int S, int K, float h, int profile, float beta,
+                float *fhat, long long out_line_step, long long out_elem_step,
+                const float *delta_in, float *delta_out, void *stream);
+
+/*
+ * Patch distances of Eq. (3) for n_lines 1-D signals of length N.
+ *   x     DEVICE; sample i of line l at x[l*stride + i] (elements of dtype).
+ *   out   DEVICE; out[(l*N + i)*(2S+1) + (s+S)] = d^2(i, i+s), s in [-S, S].
+ *         int32 when dtype == SNLM_U8 and profile == SNLM_BOX (exact integers),
+ *         float32 otherwise.
+ * Computed by the same device code as the fused passes: lifted squared
+ * differences reduced by running sums (box) or the (2K+1)-tap profile (Gaussian).
+ */
+int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride, int S, int K,
+                       int profile, float beta, void *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNLM_H */

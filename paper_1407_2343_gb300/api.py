@@ -1,0 +1,199 @@
+"""Python binding of libsnlm with the C ABI's names (argument marshalling only).
+
+Every function forwards to the entry point of the same name in libsnlm.so; all
+computation runs in the library's CUDA kernels. Device buffers are PyTorch CUDA
+tensors (used only for memory and streams); the current torch stream is used
+unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+U8, F16, F32 = 0, 1, 2
+BOX, GAUSS = 0, 1
+RC, CR, AVG, SURE = 0, 1, 2, 3
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+MAX_K, MAX_S = 7, 128
+
+_ORDERS = {"RC": RC, "CR": CR, "AVG": AVG, "SURE": SURE}
+_PROFILES = {"box": BOX, "gauss": GAUSS}
+
+
+class SnlmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {snlm_status_str(status)} ({status})")
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise SnlmError(rc, where)
+
+
+def _order(o):
+    return _ORDERS[o.upper()] if isinstance(o, str) else int(o)
+
+
+def _profile(p):
+    return _PROFILES[p.lower()] if isinstance(p, str) else int(p)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.uint8: U8, torch.float16: F16, torch.float32: F32}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}; use uint8, float16 or float32")
+    return m[t.dtype]
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def snlm_status_str(status: int) -> str:
+    return _lib.load().snlm_status_str(int(status)).decode()
+
+
+def snlm_version() -> int:
+    return int(_lib.load().snlm_version())
+
+
+def snlm_default_h(sigma: float, K: int, profile="box", beta: float = 0.0) -> float:
+    return float(_lib.load().snlm_default_h(float(sigma), int(K), _profile(profile), float(beta or 0.0)))
+
+
+def snlm_workspace_bytes(H: int, W: int, order="RC") -> int:
+    return int(_lib.load().snlm_workspace_bytes(int(H), int(W), _order(order)))
+
+
+def _image_args(img):
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("img must be a 2-D tensor with unit column stride")
+    H, W = img.shape
+    return _dtype_code(img), int(H), int(W), int(img.stride(0))
+
+
+def _h_for(h, sigma, K, profile, beta):
+    if h is None:
+        if sigma is None:
+            raise ValueError("give h or sigma")
+        h = snlm_default_h(sigma, K, profile, beta or 0.0)
+    return float(h)
+
+
+def snlm_denoise(img, S: int, K: int, h: float | None = None, profile="box", order="RC",
+                 sigma: float | None = None, beta: float = 0.0, out=None, stream=None):
+    """Separable NLM of one device image (Alg. 4 without the bilateral
+    post-filter). Returns the float32 (H, W) output tensor."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    h = _h_for(h, sigma, K, profile, beta)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    rc = _lib.load().snlm_denoise(_ptr(img), dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                  _order(order), float(sigma or 0.0), float(beta or 0.0), _ptr(out),
+                                  _stream_ptr(stream))
+    _check(rc, "snlm_denoise")
+    return out
+
+
+def snlm_denoise_ws(img, S: int, K: int, h: float | None = None, profile="box", order="RC",
+                    sigma: float | None = None, beta: float = 0.0, out=None, workspace=None,
+                    info=None, stream=None):
+    """As snlm_denoise with caller-provided scratch (a uint8 CUDA tensor of at
+    least snlm_workspace_bytes bytes) and an optional float64 `info` tensor (10)."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    h = _h_for(h, sigma, K, profile, beta)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    if workspace is None:
+        workspace = torch.empty(snlm_workspace_bytes(H, W, order), dtype=torch.uint8, device=img.device)
+    rc = _lib.load().snlm_denoise_ws(_ptr(img), dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                     _order(order), float(sigma or 0.0), float(beta or 0.0), _ptr(out),
+                                     _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                                     _ptr(info), _stream_ptr(stream))
+    _check(rc, "snlm_denoise_ws")
+    return out
+
+
+def snlm_denoise_host(img: np.ndarray, S: int, K: int, h: float | None = None, profile="box",
+                      order="RC", sigma: float | None = None, beta: float = 0.0, out: np.ndarray | None = None,
+                      stream=None) -> np.ndarray:
+    """End-to-end call on HOST arrays (numpy or pinned CPU tensors): copy in,
+    denoise, copy out; returns when the result is in `out`."""
+    torch = _torch()
+    if isinstance(img, np.ndarray):
+        codes = {np.dtype(np.uint8): U8, np.dtype(np.float16): F16, np.dtype(np.float32): F32}
+        if img.ndim != 2 or img.dtype not in codes:
+            raise TypeError("img must be a 2-D uint8/float16/float32 array")
+        a = np.ascontiguousarray(img)
+        dt, (H, W), pitch, iptr = codes[a.dtype], a.shape, a.shape[1], ctypes.c_void_p(a.ctypes.data)
+        keep = a
+    else:
+        dt, H, W, pitch = _image_args(img)
+        iptr, keep = _ptr(img), img
+    h = _h_for(h, sigma, K, profile, beta)
+    if out is None:
+        out = np.empty((H, W), np.float32)
+    optr = ctypes.c_void_p(out.ctypes.data) if isinstance(out, np.ndarray) else _ptr(out)
+    rc = _lib.load().snlm_denoise_host(iptr, dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                       _order(order), float(sigma or 0.0), float(beta or 0.0), optr,
+                                       _stream_ptr(stream) if torch.cuda.is_available() else None)
+    del keep
+    _check(rc, "snlm_denoise_host")
+    return out
+
+
+def snlm_nlm_1d(x, S: int, K: int, h: float, profile="box", beta: float = 0.0, fhat=None,
+                delta_in=None, delta_out=None, stream=None):
+    """One 1-D NLM pass (Eq. (4)) over the rows of a 2-D device tensor `x`
+    (n_lines, N) with arbitrary strides; returns fhat (float32, contiguous)."""
+    torch = _torch()
+    if x.dim() != 2:
+        raise ValueError("x must be 2-D (n_lines, N)")
+    n, N = x.shape
+    if fhat is None:
+        fhat = torch.empty((n, N), dtype=torch.float32, device=x.device)
+    for t in (delta_in, delta_out):
+        if t is not None and (t.shape != fhat.shape or t.stride() != fhat.stride() or t.dtype != torch.float32):
+            raise ValueError("delta tensors must be float32 with fhat's shape and strides")
+    rc = _lib.load().snlm_nlm_1d(_ptr(x), _dtype_code(x), int(n), int(N), int(x.stride(0)), int(x.stride(1)),
+                                 int(S), int(K), float(h), _profile(profile), float(beta or 0.0), _ptr(fhat),
+                                 int(fhat.stride(0)), int(fhat.stride(1)), _ptr(delta_in), _ptr(delta_out),
+                                 _stream_ptr(stream))
+    _check(rc, "snlm_nlm_1d")
+    return fhat
+
+
+def snlm_patch_dist_1d(x, S: int, K: int, profile="box", beta: float = 0.0, out=None, stream=None):
+    """Patch distances (Eq. (3)) of the rows of a 2-D device tensor (n, N):
+    returns (n, N, 2S+1), int32 for uint8 input with the box profile else float32."""
+    torch = _torch()
+    if x.dim() != 2 or x.stride(1) != 1:
+        raise ValueError("x must be 2-D with unit stride along lines")
+    n, N = x.shape
+    as_int = x.dtype == torch.uint8 and _profile(profile) == BOX
+    if out is None:
+        out = torch.empty((n, N, 2 * S + 1), dtype=torch.int32 if as_int else torch.float32, device=x.device)
+    rc = _lib.load().snlm_patch_dist_1d(_ptr(x), _dtype_code(x), int(n), int(N), int(x.stride(0)), int(S),
+                                        int(K), _profile(profile), float(beta or 0.0), _ptr(out),
+                                        _stream_ptr(stream))
+    _check(rc, "snlm_patch_dist_1d")
+    return out

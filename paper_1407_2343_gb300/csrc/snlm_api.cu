@@ -1,0 +1,505 @@
+// C ABI of libsnlm (declared in include/snlm.h): argument validation, scratch
+// management and the order of passes of Alg. 4 (Sec. III).
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/snlm.h"
+#include "snlm_internal.h"
+
+using namespace snlm;
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+size_t dtype_size(int dt) { return dt == SNLM_U8 ? 1 : (dt == SNLM_F16 ? 2 : 4); }
+
+bool valid_dtype(int dt) { return dt == SNLM_U8 || dt == SNLM_F16 || dt == SNLM_F32; }
+
+// A pointer the device can dereference (device or managed memory of any device).
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+double beta_or_default(float beta, int K) { return beta > 0.f ? (double)beta : (K > 0 ? K / 2.0 : 1.0); }
+
+// Profile weights g(k), k = -K..K (Sec. II, after Eq. (3)).
+void fill_profile(float *g, int K, int profile, double beta)
+{
+    for (int k = -K; k <= K; ++k)
+        g[k + K] = profile == SNLM_GAUSS ? (float)exp(-(double)k * k / (2.0 * beta * beta)) : 1.f;
+    for (int k = 2 * K + 1; k < 2 * kMaxK + 1; ++k)
+        g[k] = 0.f;
+}
+
+// exponent scale: w = 2^(c2 * d^2) = exp(-d^2 / h^2); kept finite so that
+// d^2 = 0 gives w = 1 even when h^2 underflows.
+float exp2_scale(double h)
+{
+    double c = -1.4426950408889634 / (h * h);
+    if (!(c > -3.0e38))
+        c = -3.0e38;
+    return (float)c;
+}
+
+int dist_mode_for(int dtype, int profile)
+{
+    if (profile == SNLM_GAUSS)
+        return DIST_FIR;
+    return dtype == SNLM_U8 ? DIST_SLIDE : DIST_BLOCK;
+}
+
+cudaError_t dispatch_pass(int K, const PassArgs &a, int dm, bool sure, cudaStream_t st)
+{
+    switch (K) {
+    case 0: return launch_pass<0>(a, dm, sure, st);
+    case 1: return launch_pass<1>(a, dm, sure, st);
+    case 2: return launch_pass<2>(a, dm, sure, st);
+    case 3: return launch_pass<3>(a, dm, sure, st);
+    case 4: return launch_pass<4>(a, dm, sure, st);
+    case 5: return launch_pass<5>(a, dm, sure, st);
+    case 6: return launch_pass<6>(a, dm, sure, st);
+    case 7: return launch_pass<7>(a, dm, sure, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dispatch_dist(int K, const DistArgs &a, int dm, cudaStream_t st)
+{
+    switch (K) {
+    case 0: return launch_dist<0>(a, dm, st);
+    case 1: return launch_dist<1>(a, dm, st);
+    case 2: return launch_dist<2>(a, dm, st);
+    case 3: return launch_dist<3>(a, dm, st);
+    case 4: return launch_dist<4>(a, dm, st);
+    case 5: return launch_dist<5>(a, dm, st);
+    case 6: return launch_dist<6>(a, dm, st);
+    case 7: return launch_dist<7>(a, dm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Number of CTAs of one pass over n_lines lines of length N.
+long long pass_ctas(int n_lines, int N, int S)
+{
+    return (long long)div_up(N, tile_positions(S)) * div_up(n_lines, kWarpsPerCta);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+    size_t tmp, frc, delta, part_rc, part_cr, info, total;
+    long long n_part_rc, n_part_cr;
+};
+
+// Scratch of one denoise call: the intermediate image of the first pass, f_rc
+// (AVG/SURE), the chained derivative (SURE), partial sums (SURE) and info.
+WsLayout ws_layout(int H, int W, int S, int order)
+{
+    WsLayout L;
+    const size_t img = align_up((size_t)H * W * sizeof(float), 256);
+    size_t off = 0;
+    L.tmp = off;
+    off += img;
+    L.frc = off;
+    if (order == SNLM_AVG || order == SNLM_SURE)
+        off += img;
+    L.delta = off;
+    if (order == SNLM_SURE)
+        off += img;
+    // column pass (RC's second pass) runs over W lines of length H; the row pass
+    // over H lines of length W. Size for the worst case S (smallest tiles).
+    const int Sw = S < 0 ? kMaxS : S;
+    L.n_part_rc = pass_ctas(W, H, Sw);
+    L.n_part_cr = pass_ctas(H, W, Sw);
+    L.part_rc = off;
+    if (order == SNLM_SURE)
+        off += align_up((size_t)L.n_part_rc * 4 * sizeof(double), 256);
+    L.part_cr = off;
+    if (order == SNLM_SURE)
+        off += align_up((size_t)L.n_part_cr * 4 * sizeof(double), 256);
+    L.info = off;
+    off += 256;
+    L.total = off;
+    return L;
+}
+
+// Per-device scratch pool for the calls that do not take a workspace.
+struct Pool {
+    std::mutex mu;
+    std::vector<void *> ptr;
+    std::vector<size_t> bytes;
+};
+Pool &pool()
+{
+    static Pool p;
+    return p;
+}
+
+// Returns scratch of at least `need` bytes on the current device, slot `slot`
+// (0: denoise scratch, 1: host-call input, 2: host-call output).
+void *pool_get(size_t need, int slot)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return nullptr;
+    Pool &p = pool();
+    std::lock_guard<std::mutex> g(p.mu);
+    const size_t idx = (size_t)dev * 3 + slot;
+    if (p.ptr.size() <= idx) {
+        p.ptr.resize(idx + 1, nullptr);
+        p.bytes.resize(idx + 1, 0);
+    }
+    if (p.bytes[idx] >= need)
+        return p.ptr[idx];
+    if (p.ptr[idx]) {
+        cudaDeviceSynchronize();
+        cudaFree(p.ptr[idx]);
+        p.ptr[idx] = nullptr;
+        p.bytes[idx] = 0;
+    }
+    void *q = nullptr;
+    if (cudaMalloc(&q, need) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    p.ptr[idx] = q;
+    p.bytes[idx] = need;
+    return q;
+}
+
+int check_common(int H, int W, int S, int K, float h, int profile, int order, float sigma)
+{
+    if (H < 1 || W < 1 || (long long)H * W >= (1LL << 31))
+        return SNLM_ERR_ARG;
+    if (S < 0 || S > kMaxS || K < 0)
+        return SNLM_ERR_ARG;
+    if (K > kMaxK)
+        return SNLM_ERR_UNSUPPORTED;
+    if (!(h > 0.f) || !isfinite(h))
+        return SNLM_ERR_ARG;
+    if (profile != SNLM_BOX && profile != SNLM_GAUSS)
+        return SNLM_ERR_ARG;
+    if (order < SNLM_RC || order > SNLM_SURE)
+        return SNLM_ERR_ARG;
+    if (order == SNLM_SURE) {
+        if (!(sigma >= 0.f) || !isfinite(sigma))
+            return SNLM_ERR_ARG;
+        const double h2 = (double)h * h;
+        if (!(h2 > 1e-30 && h2 < 1e30))
+            return SNLM_ERR_ARG;
+    }
+    return SNLM_OK;
+}
+
+// One pass along rows (axis 0) or columns (axis 1) of an H x W image.
+struct Pass {
+    Lines src;
+    float *dst;
+    const float *blend = nullptr;
+    const float *delta_in = nullptr;
+    float *delta_out = nullptr;
+    double *partials = nullptr;
+    Lines aux_a{nullptr, DT_F32, 0, 0};
+    Lines aux_b{nullptr, DT_F32, 0, 0};
+};
+
+cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, double h, int profile,
+                     double beta, bool sure, cudaStream_t st)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = ps.src;
+    a.n_lines = axis == 0 ? H : W;
+    a.N = axis == 0 ? W : H;
+    a.S = S;
+    a.c2 = exp2_scale(h);
+    a.h2 = (float)(h * h);
+    fill_profile(a.g, K, profile, beta);
+    a.dst = ps.dst;
+    a.out_line_step = axis == 0 ? W : 1;
+    a.out_elem_step = axis == 0 ? 1 : W;
+    a.blend = ps.blend;
+    a.delta_in = ps.delta_in;
+    a.delta_out = ps.delta_out;
+    a.partials = ps.partials;
+    a.aux_a = ps.aux_a;
+    a.aux_b = ps.aux_b;
+    return dispatch_pass(K, a, dist_mode_for(ps.src.dtype, profile), sure, st);
+}
+
+// view of a (pitched) image along rows (axis 0) or columns (axis 1)
+Lines image_lines(const void *p, int dtype, int pitch, int axis)
+{
+    return axis == 0 ? Lines{p, dtype, (long long)pitch, 1} : Lines{p, dtype, 1, (long long)pitch};
+}
+
+int status_of(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return SNLM_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return SNLM_ERR_NOMEM;
+    return SNLM_ERR_CUDA;
+}
+
+int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                 int profile, int order, float sigma, float beta, float *out, void *ws,
+                 double *info, cudaStream_t st)
+{
+    const WsLayout L = ws_layout(H, W, S, order);
+    char *base = static_cast<char *>(ws);
+    float *tmp = reinterpret_cast<float *>(base + L.tmp);
+    float *frc = reinterpret_cast<float *>(base + L.frc);
+    float *delta = reinterpret_cast<float *>(base + L.delta);
+    double *part_rc = reinterpret_cast<double *>(base + L.part_rc);
+    double *part_cr = reinterpret_cast<double *>(base + L.part_cr);
+    double *winfo = reinterpret_cast<double *>(base + L.info);
+    const double bt = beta_or_default(beta, K);
+    const bool sure = order == SNLM_SURE;
+    cudaError_t e = cudaSuccess;
+#define SNLM_TRY(x)            \
+    do {                       \
+        e = (x);               \
+        if (e != cudaSuccess)  \
+            return status_of(e); \
+    } while (0)
+
+    const Lines tmp_rows{tmp, DT_F32, (long long)W, 1};
+    const Lines tmp_cols{tmp, DT_F32, 1, (long long)W};
+    if (order == SNLM_RC) {
+        Pass p1{image_lines(img, dtype, pitch, 0), tmp};
+        SNLM_TRY(run_pass(0, H, W, p1, S, K, h, profile, bt, false, st));
+        Pass p2{tmp_cols, out};
+        SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, false, st));
+        SNLM_TRY(launch_set_theta(winfo, 1.0, 0.0, st));
+    } else if (order == SNLM_CR) {
+        Pass p1{image_lines(img, dtype, pitch, 1), tmp};
+        SNLM_TRY(run_pass(1, H, W, p1, S, K, h, profile, bt, false, st));
+        Pass p2{tmp_rows, out};
+        SNLM_TRY(run_pass(0, H, W, p2, S, K, h, profile, bt, false, st));
+        SNLM_TRY(launch_set_theta(winfo, 0.0, 1.0, st));
+    } else if (order == SNLM_AVG) {
+        Pass p1{image_lines(img, dtype, pitch, 0), tmp};
+        SNLM_TRY(run_pass(0, H, W, p1, S, K, h, profile, bt, false, st));
+        Pass p2{tmp_cols, frc};
+        SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, false, st));
+        Pass p3{image_lines(img, dtype, pitch, 1), tmp};
+        SNLM_TRY(run_pass(1, H, W, p3, S, K, h, profile, bt, false, st));
+        Pass p4{tmp_rows, out};
+        p4.blend = frc;
+        SNLM_TRY(run_pass(0, H, W, p4, S, K, h, profile, bt, false, st));
+        SNLM_TRY(launch_set_theta(winfo, 0.5, 0.5, st));
+    } else {
+        // Alg. 4: rows then columns with delta_1, columns then rows with delta_2
+        Pass p1{image_lines(img, dtype, pitch, 0), tmp};
+        p1.delta_out = delta;
+        SNLM_TRY(run_pass(0, H, W, p1, S, K, h, profile, bt, true, st));
+        Pass p2{tmp_cols, frc};
+        p2.delta_in = delta;
+        p2.partials = part_rc;
+        p2.aux_a = image_lines(img, dtype, pitch, 1);
+        SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, true, st));
+        Pass p3{image_lines(img, dtype, pitch, 1), tmp};
+        p3.delta_out = delta;
+        SNLM_TRY(run_pass(1, H, W, p3, S, K, h, profile, bt, true, st));
+        Pass p4{tmp_rows, out};
+        p4.delta_in = delta;
+        p4.partials = part_cr;
+        p4.aux_a = image_lines(img, dtype, pitch, 0);
+        p4.aux_b = Lines{frc, DT_F32, (long long)W, 1};
+        SNLM_TRY(run_pass(0, H, W, p4, S, K, h, profile, bt, true, st));
+        SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
+                                   (double)sigma * sigma, winfo, st));
+        SNLM_TRY(launch_combine(frc, out, winfo, (long long)H * W, st));
+    }
+    if (info)
+        SNLM_TRY(cudaMemcpyAsync(info, winfo, 10 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+#undef SNLM_TRY
+    return SNLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *snlm_status_str(int status)
+{
+    switch (status) {
+    case SNLM_OK: return "SNLM_OK";
+    case SNLM_ERR_ARG: return "SNLM_ERR_ARG: invalid argument";
+    case SNLM_ERR_CUDA: return "SNLM_ERR_CUDA: a CUDA call failed";
+    case SNLM_ERR_NOMEM: return "SNLM_ERR_NOMEM: out of memory";
+    case SNLM_ERR_TIMEOUT: return "SNLM_ERR_TIMEOUT: a bounded device wait gave up";
+    case SNLM_ERR_UNSUPPORTED: return "SNLM_ERR_UNSUPPORTED: configuration not compiled";
+    default: return "SNLM: unknown status";
+    }
+}
+
+int snlm_version(void) { return 100; }
+
+float snlm_default_h(float sigma, int K, int profile, float beta)
+{
+    if (!(sigma >= 0.f) || K < 0 || K > 64 || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+        return -1.f;
+    const double bt = beta_or_default(beta, K);
+    double s = 0.0;
+    for (int k = -K; k <= K; ++k)
+        s += profile == SNLM_GAUSS ? exp(-(double)k * k / (2.0 * bt * bt)) : 1.0;
+    return (float)(sigma * sqrt(s));
+}
+
+size_t snlm_workspace_bytes(int H, int W, int order)
+{
+    if (H < 1 || W < 1 || (long long)H * W >= (1LL << 31) || order < SNLM_RC || order > SNLM_SURE)
+        return 0;
+    return ws_layout(H, W, -1, order).total;
+}
+
+int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                    int profile, int order, float sigma, float beta, float *out, void *workspace,
+                    size_t workspace_bytes, double *info, void *stream)
+{
+    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (!valid_dtype(dtype) || pitch < W)
+        return SNLM_ERR_ARG;
+    if (!is_device_ptr(img) || !is_device_ptr(out) || !is_device_ptr(workspace))
+        return SNLM_ERR_ARG;
+    if (info && !is_device_ptr(info))
+        return SNLM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 15) != 0)
+        return SNLM_ERR_ARG;
+    if (workspace_bytes < ws_layout(H, W, S, order).total)
+        return SNLM_ERR_ARG;
+    return denoise_core(img, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta, out, workspace,
+                        info, static_cast<cudaStream_t>(stream));
+}
+
+int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                 int profile, int order, float sigma, float beta, float *out, void *stream)
+{
+    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (!valid_dtype(dtype) || pitch < W)
+        return SNLM_ERR_ARG;
+    if (!is_device_ptr(img) || !is_device_ptr(out))
+        return SNLM_ERR_ARG;
+    const size_t need = ws_layout(H, W, S, order).total;
+    void *ws = pool_get(need, 0);
+    if (!ws)
+        return SNLM_ERR_NOMEM;
+    return denoise_core(img, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta, out, ws, nullptr,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, int S, int K,
+                      float h, int profile, int order, float sigma, float beta, float *out_host,
+                      void *stream)
+{
+    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (!valid_dtype(dtype) || pitch < W || !img_host || !out_host)
+        return SNLM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t in_bytes = (size_t)H * pitch * dtype_size(dtype);
+    const size_t out_bytes = (size_t)H * W * sizeof(float);
+    void *din = pool_get(in_bytes, 1);
+    void *dout = pool_get(out_bytes, 2);
+    void *ws = pool_get(ws_layout(H, W, S, order).total, 0);
+    if (!din || !dout || !ws)
+        return SNLM_ERR_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(din, img_host, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return status_of(e);
+    rc = denoise_core(din, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta,
+                      static_cast<float *>(dout), ws, nullptr, st);
+    if (rc != SNLM_OK)
+        return rc;
+    e = cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess)
+        return status_of(e);
+    return status_of(cudaStreamSynchronize(st));
+}
+
+int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_step,
+                long long elem_step, int S, int K, float h, int profile, float beta, float *fhat,
+                long long out_line_step, long long out_elem_step, const float *delta_in,
+                float *delta_out, void *stream)
+{
+    if (n_lines < 1 || N < 1 || (long long)n_lines * N >= (1LL << 31) || S < 0 || S > kMaxS || K < 0)
+        return SNLM_ERR_ARG;
+    if (K > kMaxK)
+        return SNLM_ERR_UNSUPPORTED;
+    if (!valid_dtype(dtype) || !(h > 0.f) || !isfinite(h) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+        return SNLM_ERR_ARG;
+    if (!is_device_ptr(x) || !is_device_ptr(fhat))
+        return SNLM_ERR_ARG;
+    if ((delta_in && !is_device_ptr(delta_in)) || (delta_out && !is_device_ptr(delta_out)))
+        return SNLM_ERR_ARG;
+    const bool sure = delta_out != nullptr;
+    if (sure) {
+        const double h2 = (double)h * h;
+        if (!(h2 > 1e-30 && h2 < 1e30))
+            return SNLM_ERR_ARG;
+    }
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = Lines{x, dtype, line_step, elem_step};
+    a.n_lines = n_lines;
+    a.N = N;
+    a.S = S;
+    a.c2 = exp2_scale(h);
+    a.h2 = (float)((double)h * h);
+    fill_profile(a.g, K, profile, beta_or_default(beta, K));
+    a.dst = fhat;
+    a.out_line_step = out_line_step;
+    a.out_elem_step = out_elem_step;
+    a.delta_in = delta_in;
+    a.delta_out = delta_out;
+    a.aux_a = Lines{nullptr, DT_F32, 0, 0};
+    a.aux_b = Lines{nullptr, DT_F32, 0, 0};
+    return status_of(dispatch_pass(K, a, dist_mode_for(dtype, profile), sure, static_cast<cudaStream_t>(stream)));
+}
+
+int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride, int S, int K,
+                       int profile, float beta, void *out, void *stream)
+{
+    if (n_lines < 1 || N < 1 || stride < N || S < 0 || S > kMaxS || K < 0)
+        return SNLM_ERR_ARG;
+    if ((long long)n_lines * N * (2LL * S + 1) >= (1LL << 40))
+        return SNLM_ERR_ARG;
+    if (K > kMaxK)
+        return SNLM_ERR_UNSUPPORTED;
+    if (!valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+        return SNLM_ERR_ARG;
+    if (!is_device_ptr(x) || !is_device_ptr(out))
+        return SNLM_ERR_ARG;
+    DistArgs a;
+    memset(&a, 0, sizeof(a));
+    a.src = Lines{x, dtype, (long long)stride, 1};
+    a.n_lines = n_lines;
+    a.N = N;
+    a.S = S;
+    fill_profile(a.g, K, profile, beta_or_default(beta, K));
+    a.out = out;
+    a.int_out = (dtype == SNLM_U8 && profile == SNLM_BOX) ? 1 : 0;
+    return status_of(dispatch_dist(K, a, dist_mode_for(dtype, profile), static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the libsnlm translation units (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snlm {
+
+constexpr int kMaxK = 7;           // largest patch half-width compiled
+constexpr int kMaxS = 128;         // largest search half-width accepted
+constexpr int kRun = 8;            // consecutive positions a lane owns (M)
+constexpr int kChunk = 8;          // search offsets processed per register chunk (SC)
+constexpr int kWarpsPerCta = 8;    // lines per CTA (one warp per line tile)
+
+enum DType { DT_U8 = 0, DT_F16 = 1, DT_F32 = 2 };
+// How the patch distance of Eq. (3) is reduced along the line:
+//  SLIDE  running window sum (two updates per step) - exact for integer samples
+//  BLOCK  prefix/suffix sums inside blocks of 2K+1 samples (no long drift; float samples)
+//  FIR    the (2K+1)-tap weighted sum of the Gaussian profile
+enum DistMode { DIST_SLIDE = 0, DIST_BLOCK = 1, DIST_FIR = 2 };
+
+// Strided view of a set of 1-D signals: sample i of line l is at
+// ptr[l * line_step + i * elem_step] (elements of dtype).
+struct Lines {
+    const void *ptr;
+    int dtype;
+    long long line_step;
+    long long elem_step;
+};
+
+struct PassArgs {
+    Lines src;                  // input samples of the pass
+    int n_lines, N, S;
+    float c2;                   // -log2(e) / h^2, so w = 2^(c2 * d^2)
+    float h2;                   // h^2 (divergence only)
+    float g[2 * kMaxK + 1];     // patch profile g(k), k = -K..K
+    float *dst;                 // fhat, float32
+    long long out_line_step, out_elem_step;
+    const float *blend;         // optional: dst = (fhat + blend) / 2, same indexing as dst
+    const float *delta_in;      // optional (SURE kernels): chained derivative in (NULL = 1)
+    float *delta_out;           // optional (SURE kernels): chained derivative out
+    double *partials;           // optional: 4 sums per CTA (see below)
+    Lines aux_a;                // optional: image whose product with fhat is summed (sum 2)
+    Lines aux_b;                // optional: image whose product with fhat is summed (sum 1)
+    // per-CTA partial sums: [0] sum fhat^2, [1] sum fhat*aux_b, [2] sum fhat*aux_a, [3] sum delta_out
+};
+
+struct DistArgs {
+    Lines src;
+    int n_lines, N, S;
+    float g[2 * kMaxK + 1];
+    void *out;                  // (n_lines, N, 2S+1), int32 when int_out else float32
+    int int_out;
+};
+
+// Per-warp shared-memory layout of the pass and distance kernels (in floats).
+struct WarpLayout {
+    int LF;        // line samples
+    int LA;        // one mirror accumulator array (padded)
+    int kinds;     // number of mirror accumulator arrays
+    int LW;        // one stored-weight row (SURE)
+    int per_warp;  // total, multiple of 4
+};
+
+__host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// Accumulator index of relative position p: one pad word after every kRun words
+// so that lanes owning consecutive runs hit distinct banks.
+__host__ __device__ inline int acc_index(int p) { return p + p / kRun; }
+
+__host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool dist_only)
+{
+    WarpLayout L;
+    const int nch = div_up(S, kChunk);
+    L.LF = 32 * kRun + nch * kChunk + 2 * K + kChunk + 4;
+    L.LF = (L.LF + 3) & ~3;
+    L.LA = dist_only ? 0 : acc_index(32 * kRun + nch * kChunk + kChunk) + 1;
+    L.LA = (L.LA + 3) & ~3;
+    L.kinds = dist_only ? 0 : (sure ? 3 : 2);
+    L.LW = 32 * kRun;
+    int n = L.LF + L.kinds * L.LA;
+    if (sure && !dist_only)
+        n += K * L.LW + 2 * 32 * kRun;   // stored weights for |s| <= K, delta in, delta out
+    L.per_warp = (n + 3) & ~3;
+    return L;
+}
+
+// Output positions per line tile: 32 lanes minus the halo lanes that only
+// contribute mirrored pairs to the tile's first positions.
+__host__ __device__ inline int tile_positions(int S)
+{
+    return (32 - div_up(S, kRun)) * kRun;
+}
+
+template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
+template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);
+
+cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
+                              double sigma2, double *info, cudaStream_t st);
+cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info, long long n,
+                           cudaStream_t st);
+cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st);
+
+}  // namespace snlm

@@ -1,0 +1,4 @@
+// Pass and patch-distance kernels for patch half-width K = 2.
+#include "snlm_pass_impl.cuh"
+
+SNLM_INSTANTIATE_K(2)

@@ -1,0 +1,169 @@
+// SURE-optimal combination of the two separable orders (Sec. III-A, Alg. 4):
+// reduce the per-CTA partial sums of the last pass of each order, solve the 2x2
+// system A theta = b of Eqs. (19) and (25), and form theta1 f_rc + theta2 f_cr
+// (Eq. (14)).
+#include "snlm_internal.h"
+
+namespace snlm {
+
+namespace {
+
+constexpr int kSolveThreads = 256;
+
+// Sum `n` records of 4 doubles in a fixed order: thread t takes records
+// t, t + 256, ... in sequence, then a fixed binary tree over threads.
+__device__ void reduce4(const double *part, int n, double *sh, double out[4])
+{
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = 0; k < 4; ++k)
+            a[k] += part[(long long)i * 4 + k];
+    for (int k = 0; k < 4; ++k)
+        sh[k * kSolveThreads + threadIdx.x] = a[k];
+    __syncthreads();
+    for (int stride = kSolveThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride)
+            for (int k = 0; k < 4; ++k)
+                sh[k * kSolveThreads + threadIdx.x] += sh[k * kSolveThreads + threadIdx.x + stride];
+        __syncthreads();
+    }
+    for (int k = 0; k < 4; ++k)
+        out[k] = sh[k * kSolveThreads];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSolveThreads) sure_solve_kernel(const double *part_rc, int n_rc,
+                                                                   const double *part_cr, int n_cr,
+                                                                   double sigma2, double *info)
+{
+    __shared__ double sh[4 * kSolveThreads];
+    double rc[4], cr[4];
+    // records: [0] sum fhat^2, [1] sum fhat*aux_b, [2] sum fhat*f, [3] sum delta
+    reduce4(part_rc, n_rc, sh, rc);
+    reduce4(part_cr, n_cr, sh, cr);
+    if (threadIdx.x != 0)
+        return;
+    const double a = rc[0], c = cr[1], e = cr[0];
+    const double b0 = rc[2] - sigma2 * rc[3];
+    const double b1 = cr[2] - sigma2 * cr[3];
+    double t0, t1;
+    const double det = a * e - c * c, tr = a + e;
+    if (det > 1e-12 * tr * tr) {
+        t0 = (e * b0 - c * b1) / det;
+        t1 = (a * b1 - c * b0) / det;
+    } else {
+        // minimum-norm solution: project on the dominant eigenvector
+        const double half = 0.5 * (a - e);
+        const double lam = 0.5 * tr + sqrt(half * half + c * c);
+        if (!(lam > 0.0)) {
+            t0 = t1 = 0.0;
+        } else {
+            double v0, v1;
+            if (fabs(c) > 0.0) {
+                v0 = c;
+                v1 = lam - a;
+            } else if (a >= e) {
+                v0 = 1.0;
+                v1 = 0.0;
+            } else {
+                v0 = 0.0;
+                v1 = 1.0;
+            }
+            const double nv = sqrt(v0 * v0 + v1 * v1);
+            v0 /= nv;
+            v1 /= nv;
+            const double coef = (v0 * b0 + v1 * b1) / lam;
+            t0 = coef * v0;
+            t1 = coef * v1;
+        }
+    }
+    info[0] = t0;
+    info[1] = t1;
+    info[2] = a;
+    info[3] = c;
+    info[4] = e;
+    info[5] = rc[2];
+    info[6] = cr[2];
+    info[7] = rc[3];
+    info[8] = cr[3];
+    info[9] = sigma2;
+}
+
+// out = theta1 * frc + theta2 * out, with theta split into float hi + lo parts so
+// the weights keep ~48 bits.
+__global__ void combine_kernel(const float4 *__restrict__ frc, float4 *__restrict__ out,
+                               const double *__restrict__ info, long long n4)
+{
+    const double t0 = info[0], t1 = info[1];
+    const float h0 = (float)t0, h1 = (float)t1;
+    const float l0 = (float)(t0 - (double)h0), l1 = (float)(t1 - (double)h1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = frc[i];
+        float4 b = out[i];
+        b.x = fmaf(h0, a.x, fmaf(h1, b.x, fmaf(l0, a.x, l1 * b.x)));
+        b.y = fmaf(h0, a.y, fmaf(h1, b.y, fmaf(l0, a.y, l1 * b.y)));
+        b.z = fmaf(h0, a.z, fmaf(h1, b.z, fmaf(l0, a.z, l1 * b.z)));
+        b.w = fmaf(h0, a.w, fmaf(h1, b.w, fmaf(l0, a.w, l1 * b.w)));
+        out[i] = b;
+    }
+}
+
+__global__ void combine_scalar_kernel(const float *__restrict__ frc, float *__restrict__ out,
+                                      const double *__restrict__ info, long long start, long long n)
+{
+    const double t0 = info[0], t1 = info[1];
+    const float h0 = (float)t0, h1 = (float)t1;
+    const float l0 = (float)(t0 - (double)h0), l1 = (float)(t1 - (double)h1);
+    for (long long i = start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = fmaf(h0, frc[i], fmaf(h1, out[i], fmaf(l0, frc[i], l1 * out[i])));
+}
+
+__global__ void set_theta_kernel(double *info, double t0, double t1)
+{
+    if (threadIdx.x < 10)
+        info[threadIdx.x] = threadIdx.x == 0 ? t0 : (threadIdx.x == 1 ? t1 : 0.0);
+}
+
+}  // namespace
+
+cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
+                              double sigma2, double *info, cudaStream_t st)
+{
+    sure_solve_kernel<<<1, kSolveThreads, 0, st>>>(part_rc, n_rc, part_cr, n_cr, sigma2, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info, long long n,
+                           cudaStream_t st)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(frc) | reinterpret_cast<uintptr_t>(out_fcr)) & 15) == 0;
+    const long long n4 = aligned ? n / 4 : 0;
+    if (n4 > 0) {
+        long long blocks = (n4 + 255) / 256;
+        if (blocks > (long long)sms * 8)
+            blocks = (long long)sms * 8;
+        combine_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(frc),
+                                                         reinterpret_cast<float4 *>(out_fcr), info, n4);
+    }
+    const long long rest = n - n4 * 4;
+    if (rest > 0) {
+        long long blocks = (rest + 255) / 256;
+        if (blocks > (long long)sms * 8)
+            blocks = (long long)sms * 8;
+        combine_scalar_kernel<<<(unsigned)blocks, 256, 0, st>>>(frc, out_fcr, info, n4 * 4, n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st)
+{
+    set_theta_kernel<<<1, 32, 0, st>>>(info, t1, t2);
+    return cudaGetLastError();
+}
+
+}  // namespace snlm
