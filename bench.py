@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the separable NLM hot path (Alg. 4 of Ghosh & Chaudhury,
+arXiv:1407.2343) on one or more GPUs of one node.
+
+A step is one snlm_denoise of a 4096x4096 uint8 synthetic noisy scene (sigma =
+30, S = 20, K = 5, box profile, h = sigma*sqrt(2K+1)) in the SURE order: the four
+1-D passes of Alg. 4 with the chained divergence, the 2x2 solve and the
+combination. Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MiB write) between timed steps, outside the per-step events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank denoises its own image
+(weak scaling, no data-path collective); value = all ranks' pixels / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "denoised Mpixel/s and lifted patch-pairs/s vs roofline; batched/served vs plain, p50/p99"
+
+# GB300: 152 SMs, 2070 MHz maximum SM clock; per SM per clock: 128 FP32 lanes
+# (FADD/FMUL/FFMA each one lane-operation) and 32 MUFU.EX2 results.
+SMS, MAX_MHZ = 152, 2070.0
+ALU_PEAK_TOPS = SMS * 128 * MAX_MHZ * 1e6 / 1e12
+SFU_PEAK_TEXP = SMS * 32 * MAX_MHZ * 1e6 / 1e12
+# Algorithmic FP32 operations per unique pair (x, x+s) of one 1-D pass: lift (sub,
+# mul) 2, box reduction (add new, remove old) 2, exponent scale 1, accumulation into
+# both pixels 4 (two FMA, two adds); the divergence passes add the weighted squared
+# differences of both pixels, 2 more. One MUFU ex2 per unique pair.
+OPS_PER_PAIR = {"plain": 9, "sure": 11}
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
+# for the kernel sources whose hash is recorded with it (see profiles/).
+TRAFFIC = {"sources_sha": None, "kernel": None, "bytes_per_launch": None}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1407_2343_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--S", type=int, default=20)
+    ap.add_argument("--K", type=int, default=5)
+    ap.add_argument("--sigma", type=float, default=30.0)
+    ap.add_argument("--dtype", default="u8", choices=["u8", "f16", "f32"])
+    ap.add_argument("--order", default="SURE", choices=["RC", "CR", "AVG", "SURE"])
+    ap.add_argument("--profile", default="box", choices=["box", "gauss"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rc", action="store_true", help="skip the extra RC-order measurement")
+    return ap.parse_args()
+
+
+def workload(a):
+    return {"workload": f"{a.size}x{a.size} {a.dtype} synthetic scene (20 shapes + texture + "
+                        f"N(0,{a.sigma:g}^2)), S={a.S}, K={a.K}, {a.profile} profile, "
+                        f"h=sigma*sqrt(sum g), order {a.order} (Alg. 4)",
+            "H": a.size, "W": a.size, "S": a.S, "K": a.K, "sigma": a.sigma, "profile": a.profile,
+            "order": a.order, "storage": a.dtype, "seed": 0,
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)"}
+
+
+def passes_of(order):
+    return 2 if order in ("RC", "CR") else 4
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"snlm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(a, target_s: float):
+    """Time the FP64 oracle (as it stands) on a bounded crop of the workload's
+    scene on the host cores; returns (Mpixel/s, cores, description)."""
+    import oracle
+    from paper_1407_2343_gb300 import synth
+
+    oracle.build()
+    img = synth.noisy_image(a.size, a.size, a.sigma, seed=0, dtype=a.dtype).astype(np.float64)
+    h = oracle.default_h(a.sigma, a.K, a.profile)
+    cores = oracle.max_threads()
+    side = 128
+    t0 = time.perf_counter()
+    oracle.snlm(img[:side, :side], a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    t_cal = time.perf_counter() - t0
+    side = int(min(a.size, max(128, side * math.sqrt(target_s / max(t_cal, 1e-4)))))
+    crop = img[:side, :side]
+    t0 = time.perf_counter()
+    oracle.snlm(crop, a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    dt = time.perf_counter() - t0
+    return side * side / dt / 1e6, cores, f"{side}x{side} top-left crop of the same scene, one Alg. 4 run ({dt:.2f} s)", side, dt
+
+
+def run_reference(a):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1407_2343_gb300 import synth
+
+    oracle.build()
+    img = synth.noisy_image(a.size, a.size, a.sigma, seed=0, dtype=a.dtype).astype(np.float64)
+    h = oracle.default_h(a.sigma, a.K, a.profile)
+    cores = oracle.max_threads()
+    # size each step so that the whole run takes about two minutes
+    budget = 120.0 / max(1, a.steps + a.warmup)
+    side = 96
+    t0 = time.perf_counter()
+    oracle.snlm(img[:side, :side], a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    t_cal = time.perf_counter() - t0
+    side = int(min(a.size, max(64, side * math.sqrt(budget / max(t_cal, 1e-4)))))
+    crop = img[:side, :side]
+    for _ in range(a.warmup):
+        oracle.snlm(crop, a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.snlm(crop, a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    dt = time.perf_counter() - t0
+    value = a.steps * side * side / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(a),
+            "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{side}x{side} top-left crop of the same scene per step"},
+            "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1407_2343_gb300 import _lib, api, synth
+
+    _lib.load(build_if_missing=True)
+    img_np = synth.noisy_image(a.size, a.size, a.sigma, seed=rank, dtype=a.dtype)
+    img = torch.from_numpy(img_np).to(dev)
+    H = W = a.size
+    h = api.snlm_default_h(a.sigma, a.K, a.profile)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    ws = torch.empty(api.snlm_workspace_bytes(H, W, a.order), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(order=a.order):
+        api.snlm_denoise_ws(img, a.S, a.K, h, a.profile, order, a.sigma, out=out, workspace=ws, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def timed(order, steps, clocks=None):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        api.snlm_trace_read()
+        api.snlm_trace_enable(True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        w0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step(order)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - w0
+        ck = clocks.stop() if clocks else None
+        api.snlm_trace_enable(False)
+        trace = api.snlm_trace_read(1 << 20)
+        dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        return dev_ms, wall, trace, ck
+
+    dev_ms, wall, trace, clocks = timed(a.order, a.steps, Clocks(local))
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    dev_ms_max = float(t_max.item())
+    px = H * W
+    value = world * a.steps * px / (dev_ms_max * 1e-3) / 1e6
+    npass = passes_of(a.order)
+    pairs_paper = world * a.steps * npass * px * (2 * a.S + 1) / (dev_ms_max * 1e-3)
+
+    # per-kernel times from the launch trace (CUDA events on the launching stream)
+    per = {}
+    for name, ms in trace:
+        d = per.setdefault(name, [0, 0.0])
+        d[0] += 1
+        d[1] += ms
+    total_k = sum(v[1] for v in per.values()) or 1.0
+    kernels = {k: {"launches": v[0], "total_ms": v[1], "avg_ms": v[1] / v[0], "share": v[1] / total_k}
+               for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])}
+    dom = max(per.items(), key=lambda kv: kv[1][1])[0]
+    avg_s = per[dom][1] / per[dom][0] * 1e-3
+    kind = "sure" if dom.endswith("_sure") else "plain"
+    pairs_launch = px * a.S
+    achieved = OPS_PER_PAIR[kind] * pairs_launch / avg_s / 1e12
+    traffic = None
+    if TRAFFIC["sources_sha"] == kernel_sources_sha() and TRAFFIC["kernel"] == dom:
+        traffic = TRAFFIC["bytes_per_launch"]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ALU_PEAK_TOPS,
+                "unit": "Tops/s (FP32 lane-ops)", "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
+                "ops_per_unique_pair": OPS_PER_PAIR[kind], "unique_pairs_per_launch": pairs_launch,
+                "avg_launch_ms": avg_s * 1e3,
+                "sfu": {"achieved_Texp_s": pairs_launch / avg_s / 1e12, "peak_Texp_s": SFU_PEAK_TEXP,
+                        "frac": pairs_launch / avg_s / 1e12 / SFU_PEAK_TEXP},
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and maximum clock)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dev_ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload(a), parallelism=f"replicas{world}" if world > 1 else "single"),
+            "pairs_per_s": pairs_paper, "unique_pairs_per_s": pairs_paper * a.S / (2 * a.S + 1),
+            "wall_s_timed_region": wall, "roofline": roofline, "kernels": kernels,
+            "gpu_launches": len(trace), "clocks": clocks}
+
+    if not a.no_rc and a.order != "RC":
+        ms_rc, _, tr_rc, _ = timed("RC", max(20, a.steps // 4))
+        n_rc = max(20, a.steps // 4)
+        line["rc_order"] = {"Mpixel_s": world * n_rc * px / (ms_rc * 1e-3) / 1e6, "ms_per_step": ms_rc / n_rc,
+                            "gpu_launches": len(tr_rc)}
+
+    if not a.no_e2e:
+        host_in = torch.from_numpy(img_np).pin_memory()
+        host_out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            api.snlm_denoise_host(host_in, a.S, a.K, h, a.profile, a.order, a.sigma, out=host_out, stream=stream)
+        n_e2e = max(10, a.steps // 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            api.snlm_denoise_host(host_in, a.S, a.K, h, a.profile, a.order, a.sigma, out=host_out, stream=stream)
+        t_e2e = time.perf_counter() - t0
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        line["e2e"] = {"value": world * n_e2e * px / float(t.item()) / 1e6, "unit": "Mpixel/s",
+                       "h2d_bytes_per_step": int(img_np.nbytes), "d2h_bytes_per_step": int(H * W * 4),
+                       "steps": n_e2e, "api": "snlm_denoise_host (pinned host buffers)"}
+
+    if rank == 0 and not a.no_cpu_baseline:
+        v, cores, desc, _, _ = cpu_oracle_rate(a, target_s=6.0)
+        line["cpu_baseline"] = {"value": v, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

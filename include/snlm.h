@@ -143,6 +143,33 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
 int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride, int S, int K,
                        int profile, float beta, void *out, void *stream);
 
+
+/*
+ * Launch tracing (no counterpart in the paper; for profiling). When enabled,
+ * every kernel the library launches is bracketed by two CUDA events recorded on
+ * the launching stream, and snlm_trace_read returns one record per launch:
+ * kinds[i] (an snlm_kernel_kind) and ms[i] (device time between the events).
+ * Tracing is process-wide; do not enable it while a stream is being captured
+ * into a CUDA graph. snlm_trace_read waits for the recorded events, copies at
+ * most max_records records (oldest first), sets *n_records to the number copied
+ * and clears the trace. snlm_trace_enable returns the previous setting.
+ */
+typedef enum {
+    SNLM_K_ROW_PASS = 0,       /* 1-D NLM pass along rows (Eq. (4)) */
+    SNLM_K_COL_PASS = 1,       /* 1-D NLM pass along columns */
+    SNLM_K_ROW_PASS_SURE = 2,  /* row pass with the divergence of Eq. (24) */
+    SNLM_K_COL_PASS_SURE = 3,  /* column pass with the divergence of Eq. (24) */
+    SNLM_K_SURE_SOLVE = 4,     /* reduction of the sums of Eqs. (19), (25) and the 2x2 solve */
+    SNLM_K_COMBINE = 5,        /* theta1 f_rc + theta2 f_cr (Eq. (14)) */
+    SNLM_K_SET_THETA = 6,      /* writes the fixed weights of the RC / CR / AVG orders */
+    SNLM_K_PATCH_DIST = 7,     /* patch distances of Eq. (3) */
+    SNLM_K_LINE_PASS = 8       /* snlm_nlm_1d pass over arbitrary strided lines */
+} snlm_kernel_kind;
+
+int snlm_trace_enable(int enable);
+int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records);
+const char *snlm_kernel_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

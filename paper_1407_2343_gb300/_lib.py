@@ -56,6 +56,12 @@ def load(build_if_missing: bool = False):
         lib.snlm_nlm_1d.restype = ci
         lib.snlm_patch_dist_1d.argtypes = [vp, ci, ci, ci, ci, ci, ci, ci, cf, vp, vp]
         lib.snlm_patch_dist_1d.restype = ci
+        lib.snlm_trace_enable.argtypes = [ci]
+        lib.snlm_trace_enable.restype = ci
+        lib.snlm_trace_read.argtypes = [ctypes.POINTER(ci), fp, ci, ctypes.POINTER(ci)]
+        lib.snlm_trace_read.restype = ci
+        lib.snlm_kernel_name.argtypes = [ci]
+        lib.snlm_kernel_name.restype = ctypes.c_char_p
         del fp, dp
         _lib = lib
         return lib
@@ -64,5 +70,6 @@ def load(build_if_missing: bool = False):
 # names declared in include/snlm.h (checked by the ABI test)
 EXPORTED = [
     "snlm_status_str", "snlm_version", "snlm_default_h", "snlm_workspace_bytes", "snlm_denoise",
-    "snlm_denoise_ws", "snlm_denoise_host", "snlm_nlm_1d", "snlm_patch_dist_1d",
+    "snlm_denoise_ws", "snlm_denoise_host", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
+    "snlm_trace_read", "snlm_kernel_name",
 ]

@@ -197,3 +197,22 @@ def snlm_patch_dist_1d(x, S: int, K: int, profile="box", beta: float = 0.0, out=
                                         _stream_ptr(stream))
     _check(rc, "snlm_patch_dist_1d")
     return out
+
+
+def snlm_trace_enable(enable: bool = True) -> bool:
+    """Bracket every library kernel launch with CUDA events (process-wide)."""
+    return bool(_lib.load().snlm_trace_enable(1 if enable else 0))
+
+
+def snlm_trace_read(max_records: int = 1 << 16):
+    """Per-launch device times since the last read: list of (kernel_name, ms)."""
+    lib = _lib.load()
+    kinds = (ctypes.c_int * max_records)()
+    ms = (ctypes.c_float * max_records)()
+    n = ctypes.c_int(0)
+    _check(lib.snlm_trace_read(kinds, ms, max_records, ctypes.byref(n)), "snlm_trace_read")
+    return [(lib.snlm_kernel_name(kinds[i]).decode(), float(ms[i])) for i in range(n.value)]
+
+
+def snlm_kernel_name(kind: int) -> str:
+    return _lib.load().snlm_kernel_name(int(kind)).decode()

@@ -126,15 +126,77 @@ WsLayout ws_layout(int H, int W, int S, int order)
     L.n_part_cr = pass_ctas(H, W, Sw);
     L.part_rc = off;
     if (order == SNLM_SURE)
-        off += align_up((size_t)L.n_part_rc * 4 * sizeof(double), 256);
+        off += align_up((size_t)L.n_part_rc * kPartials * sizeof(double), 256);
     L.part_cr = off;
     if (order == SNLM_SURE)
-        off += align_up((size_t)L.n_part_cr * 4 * sizeof(double), 256);
+        off += align_up((size_t)L.n_part_cr * kPartials * sizeof(double), 256);
     L.info = off;
     off += 256;
     L.total = off;
     return L;
 }
+
+
+// ------------------------------------------------------------------ launch tracing
+
+struct TraceRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+struct Trace {
+    std::mutex mu;
+    bool on = false;
+    std::vector<TraceRec> recs;
+    std::vector<cudaEvent_t> spare;
+};
+Trace &trace()
+{
+    static Trace t;
+    return t;
+}
+
+cudaEvent_t trace_event(Trace &t)
+{
+    if (!t.spare.empty()) {
+        cudaEvent_t e = t.spare.back();
+        t.spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one launch with events when tracing is on.
+struct TraceScope {
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool active = false;
+    TraceScope(int k, cudaStream_t s) : kind(k), st(s)
+    {
+        Trace &t = trace();
+        std::lock_guard<std::mutex> g(t.mu);
+        if (!t.on)
+            return;
+        a = trace_event(t);
+        b = trace_event(t);
+        if (a && b && cudaEventRecord(a, st) == cudaSuccess)
+            active = true;
+    }
+    ~TraceScope()
+    {
+        if (!active)
+            return;
+        Trace &t = trace();
+        std::lock_guard<std::mutex> g(t.mu);
+        if (cudaEventRecord(b, st) == cudaSuccess)
+            t.recs.push_back({kind, a, b});
+    }
+};
 
 // Per-device scratch pool for the calls that do not take a workspace.
 struct Pool {
@@ -212,8 +274,8 @@ struct Pass {
     const float *delta_in = nullptr;
     float *delta_out = nullptr;
     double *partials = nullptr;
-    Lines aux_a{nullptr, DT_F32, 0, 0};
-    Lines aux_b{nullptr, DT_F32, 0, 0};
+    Lines aux_f{nullptr, DT_F32, 0, 0};
+    Lines aux_rc{nullptr, DT_F32, 0, 0};
 };
 
 cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, double h, int profile,
@@ -235,8 +297,9 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     a.delta_in = ps.delta_in;
     a.delta_out = ps.delta_out;
     a.partials = ps.partials;
-    a.aux_a = ps.aux_a;
-    a.aux_b = ps.aux_b;
+    a.aux_f = ps.aux_f;
+    a.aux_rc = ps.aux_rc;
+    TraceScope ts((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) + (sure ? 2 : 0), st);
     return dispatch_pass(K, a, dist_mode_for(ps.src.dtype, profile), sure, st);
 }
 
@@ -284,12 +347,14 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         SNLM_TRY(run_pass(0, H, W, p1, S, K, h, profile, bt, false, st));
         Pass p2{tmp_cols, out};
         SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, false, st));
+        TraceScope ts(SNLM_K_SET_THETA, st);
         SNLM_TRY(launch_set_theta(winfo, 1.0, 0.0, st));
     } else if (order == SNLM_CR) {
         Pass p1{image_lines(img, dtype, pitch, 1), tmp};
         SNLM_TRY(run_pass(1, H, W, p1, S, K, h, profile, bt, false, st));
         Pass p2{tmp_rows, out};
         SNLM_TRY(run_pass(0, H, W, p2, S, K, h, profile, bt, false, st));
+        TraceScope ts(SNLM_K_SET_THETA, st);
         SNLM_TRY(launch_set_theta(winfo, 0.0, 1.0, st));
     } else if (order == SNLM_AVG) {
         Pass p1{image_lines(img, dtype, pitch, 0), tmp};
@@ -301,6 +366,7 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         Pass p4{tmp_rows, out};
         p4.blend = frc;
         SNLM_TRY(run_pass(0, H, W, p4, S, K, h, profile, bt, false, st));
+        TraceScope ts(SNLM_K_SET_THETA, st);
         SNLM_TRY(launch_set_theta(winfo, 0.5, 0.5, st));
     } else {
         // Alg. 4: rows then columns with delta_1, columns then rows with delta_2
@@ -310,7 +376,6 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         Pass p2{tmp_cols, frc};
         p2.delta_in = delta;
         p2.partials = part_rc;
-        p2.aux_a = image_lines(img, dtype, pitch, 1);
         SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, true, st));
         Pass p3{image_lines(img, dtype, pitch, 1), tmp};
         p3.delta_out = delta;
@@ -318,12 +383,18 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         Pass p4{tmp_rows, out};
         p4.delta_in = delta;
         p4.partials = part_cr;
-        p4.aux_a = image_lines(img, dtype, pitch, 0);
-        p4.aux_b = Lines{frc, DT_F32, (long long)W, 1};
+        p4.aux_f = image_lines(img, dtype, pitch, 0);
+        p4.aux_rc = Lines{frc, DT_F32, (long long)W, 1};
         SNLM_TRY(run_pass(0, H, W, p4, S, K, h, profile, bt, true, st));
-        SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
-                                   (double)sigma * sigma, winfo, st));
-        SNLM_TRY(launch_combine(frc, out, winfo, (long long)H * W, st));
+        {
+            TraceScope ts(SNLM_K_SURE_SOLVE, st);
+            SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
+                                       (double)sigma * sigma, winfo, st));
+        }
+        {
+            TraceScope ts(SNLM_K_COMBINE, st);
+            SNLM_TRY(launch_combine(frc, out, winfo, (long long)H * W, st));
+        }
     }
     if (info)
         SNLM_TRY(cudaMemcpyAsync(info, winfo, 10 * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -472,8 +543,9 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
     a.out_elem_step = out_elem_step;
     a.delta_in = delta_in;
     a.delta_out = delta_out;
-    a.aux_a = Lines{nullptr, DT_F32, 0, 0};
-    a.aux_b = Lines{nullptr, DT_F32, 0, 0};
+    a.aux_f = Lines{nullptr, DT_F32, 0, 0};
+    a.aux_rc = Lines{nullptr, DT_F32, 0, 0};
+    TraceScope ts(SNLM_K_LINE_PASS, static_cast<cudaStream_t>(stream));
     return status_of(dispatch_pass(K, a, dist_mode_for(dtype, profile), sure, static_cast<cudaStream_t>(stream)));
 }
 
@@ -499,7 +571,60 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
     fill_profile(a.g, K, profile, beta_or_default(beta, K));
     a.out = out;
     a.int_out = (dtype == SNLM_U8 && profile == SNLM_BOX) ? 1 : 0;
+    TraceScope ts(SNLM_K_PATCH_DIST, static_cast<cudaStream_t>(stream));
     return status_of(dispatch_dist(K, a, dist_mode_for(dtype, profile), static_cast<cudaStream_t>(stream)));
+}
+
+int snlm_trace_enable(int enable)
+{
+    Trace &t = trace();
+    std::lock_guard<std::mutex> g(t.mu);
+    const int prev = t.on ? 1 : 0;
+    t.on = enable != 0;
+    return prev;
+}
+
+int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records)
+{
+    if (max_records < 0 || (max_records > 0 && (!kinds || !ms)) || !n_records)
+        return SNLM_ERR_ARG;
+    Trace &t = trace();
+    std::lock_guard<std::mutex> g(t.mu);
+    int n = 0;
+    int rc = SNLM_OK;
+    for (const TraceRec &r : t.recs) {
+        if (n < max_records) {
+            float v = -1.f;
+            if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&v, r.a, r.b) != cudaSuccess) {
+                cudaGetLastError();
+                rc = SNLM_ERR_CUDA;
+            }
+            kinds[n] = r.kind;
+            ms[n] = v;
+            ++n;
+        }
+        t.spare.push_back(r.a);
+        t.spare.push_back(r.b);
+    }
+    t.recs.clear();
+    *n_records = n;
+    return rc;
+}
+
+const char *snlm_kernel_name(int kind)
+{
+    switch (kind) {
+    case SNLM_K_ROW_PASS: return "row_pass";
+    case SNLM_K_COL_PASS: return "col_pass";
+    case SNLM_K_ROW_PASS_SURE: return "row_pass_sure";
+    case SNLM_K_COL_PASS_SURE: return "col_pass_sure";
+    case SNLM_K_SURE_SOLVE: return "sure_solve";
+    case SNLM_K_COMBINE: return "combine";
+    case SNLM_K_SET_THETA: return "set_theta";
+    case SNLM_K_PATCH_DIST: return "patch_dist";
+    case SNLM_K_LINE_PASS: return "line_pass";
+    default: return "unknown";
+    }
 }
 
 }  // extern "C"

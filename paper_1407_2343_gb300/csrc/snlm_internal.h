@@ -11,6 +11,7 @@ constexpr int kMaxS = 128;         // largest search half-width accepted
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
 constexpr int kChunk = 8;          // search offsets processed per register chunk (SC)
 constexpr int kWarpsPerCta = 8;    // lines per CTA (one warp per line tile)
+constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
 
 enum DType { DT_U8 = 0, DT_F16 = 1, DT_F32 = 2 };
 // How the patch distance of Eq. (3) is reduced along the line:
@@ -39,10 +40,12 @@ struct PassArgs {
     const float *blend;         // optional: dst = (fhat + blend) / 2, same indexing as dst
     const float *delta_in;      // optional (SURE kernels): chained derivative in (NULL = 1)
     float *delta_out;           // optional (SURE kernels): chained derivative out
-    double *partials;           // optional: 4 sums per CTA (see below)
-    Lines aux_a;                // optional: image whose product with fhat is summed (sum 2)
-    Lines aux_b;                // optional: image whose product with fhat is summed (sum 1)
-    // per-CTA partial sums: [0] sum fhat^2, [1] sum fhat*aux_b, [2] sum fhat*aux_a, [3] sum delta_out
+    double *partials;           // optional: kPartials sums per CTA (see below)
+    Lines aux_f;                // the noisy input image f, viewed like dst
+    Lines aux_rc;               // f_rc, viewed like dst: when given, the SURE sums below are formed
+    // Per-CTA partial sums (SURE). With m = (f_rc + fhat)/2 and d = (f_rc - fhat)/2
+    // (fhat = f_cr in the last pass of the CR order):
+    //   [0] sum m^2  [1] sum m d  [2] sum d^2  [3] sum f m  [4] sum f d  [5] sum delta_out
 };
 
 struct DistArgs {

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
     __syncthreads();
 
     // ---- store: fhat (optionally blended), delta_out, partial sums
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool row_like = p.out_elem_step == 1;
     const int total = kWarpsPerCta * T;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -329,39 +329,44 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
             const float dv = wb[(dst_d - fl) + q];
             if (p.delta_out)
                 p.delta_out[o] = dv;
-            s3 += dv;
-        }
-        if (p.partials) {
-            s0 = fmaf(v, v, s0);
-            if (p.aux_b.ptr)
-                s1 = fmaf(v, load_sample(p.aux_b, ln, x), s1);
-            if (p.aux_a.ptr)
-                s2 = fmaf(v, load_sample(p.aux_a, ln, x), s2);
+            s[5] += dv;
+            if (p.aux_rc.ptr) {
+                // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
+                const float rc = load_sample(p.aux_rc, ln, x);
+                const float fv = load_sample(p.aux_f, ln, x);
+                const float mm = 0.5f * (rc + v), dd = 0.5f * (rc - v);
+                s[0] = fmaf(mm, mm, s[0]);
+                s[1] = fmaf(mm, dd, s[1]);
+                s[2] = fmaf(dd, dd, s[2]);
+                s[3] = fmaf(fv, mm, s[3]);
+                s[4] = fmaf(fv, dd, s[4]);
+            }
         }
     }
-    if (p.partials) {
-        // deterministic reduction: fp64 warp tree, then warps in order
-        double d0 = s0, d1 = s1, d2 = s2, d3 = s3;
+    if constexpr (SURE) {
+        if (p.partials) {
+            // deterministic reduction: fp64 warp tree, then warps in order
+            double d[6];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            d0 += __shfl_down_sync(0xffffffffu, d0, o);
-            d1 += __shfl_down_sync(0xffffffffu, d1, o);
-            d2 += __shfl_down_sync(0xffffffffu, d2, o);
-            d3 += __shfl_down_sync(0xffffffffu, d3, o);
-        }
-        __shared__ double red[kWarpsPerCta][4];
-        if (lane == 0) {
-            red[wid][0] = d0;
-            red[wid][1] = d1;
-            red[wid][2] = d2;
-            red[wid][3] = d3;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double t = 0.0;
-            for (int w = 0; w < kWarpsPerCta; ++w)
-                t += red[w][threadIdx.x];
-            p.partials[(long long)blockIdx.x * 4 + threadIdx.x] = t;
+            for (int k = 0; k < 6; ++k) {
+                d[k] = s[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+            }
+            __shared__ double red[kWarpsPerCta][6];
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    red[wid][k] = d[k];
+            __syncthreads();
+            if (threadIdx.x < kPartials) {
+                double t = 0.0;
+                if (threadIdx.x < 6)
+                    for (int w = 0; w < kWarpsPerCta; ++w)
+                        t += red[w][threadIdx.x];
+                p.partials[(long long)blockIdx.x * kPartials + threadIdx.x] = t;
+            }
         }
     }
 }
