@@ -279,7 +279,7 @@ def run_ours(a):
                for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])}
     dom = max(per.items(), key=lambda kv: kv[1][1])[0]
     avg_s = per[dom][1] / per[dom][0] * 1e-3
-    kind = "sure" if dom.endswith("_sure") else "plain"
+    kind = "sure" if "_sure" in dom else "plain"
     pairs_launch = px * a.S
     achieved = OPS_PER_PAIR[kind] * pairs_launch / avg_s / 1e12
     traffic = None

@@ -21,7 +21,8 @@
  *    f(N) = f(N-1)), repeated with period 2N when S + K >= N; it applies to the
  *    samples of a patch and to search positions alike.
  *  - Limits: 0 <= K <= SNLM_MAX_K, 0 <= S <= SNLM_MAX_S, H, W >= 1,
- *    H * W < 2^31, h > 0 and finite.
+ *    H * W < 2^31 and H * pitch < 2^31 (element offsets are 32-bit), h > 0 and
+ *    finite. Strides are positive.
  */
 #ifndef SNLM_H
 #define SNLM_H
@@ -149,6 +150,9 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
  * every kernel the library launches is bracketed by two CUDA events recorded on
  * the launching stream, and snlm_trace_read returns one record per launch:
  * kinds[i] (an snlm_kernel_kind) and ms[i] (device time between the events).
+ * The low byte of a kind is an snlm_kernel_kind; bits 8 and up tell how the
+ * patch distances were reduced in that launch (0 running sum, 1 block sums,
+ * 2 weighted taps); snlm_kernel_name spells both out (e.g. "row_pass/slide").
  * Tracing is process-wide; do not enable it while a stream is being captured
  * into a CUDA graph. snlm_trace_read waits for the recorded events, copies at
  * most max_records records (oldest first), sets *n_records to the number copied

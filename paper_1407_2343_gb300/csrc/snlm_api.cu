@@ -299,8 +299,9 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     a.partials = ps.partials;
     a.aux_f = ps.aux_f;
     a.aux_rc = ps.aux_rc;
-    TraceScope ts((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) + (sure ? 2 : 0), st);
-    return dispatch_pass(K, a, dist_mode_for(ps.src.dtype, profile), sure, st);
+    const int dm = dist_mode_for(ps.src.dtype, profile);
+    TraceScope ts(((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) + (sure ? 2 : 0)) | (dm << 8), st);
+    return dispatch_pass(K, a, dm, sure, st);
 }
 
 // view of a (pitched) image along rows (axis 0) or columns (axis 1)
@@ -446,7 +447,7 @@ int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, 
     int rc = check_common(H, W, S, K, h, profile, order, sigma);
     if (rc != SNLM_OK)
         return rc;
-    if (!valid_dtype(dtype) || pitch < W)
+    if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31))
         return SNLM_ERR_ARG;
     if (!is_device_ptr(img) || !is_device_ptr(out) || !is_device_ptr(workspace))
         return SNLM_ERR_ARG;
@@ -466,7 +467,7 @@ int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int
     int rc = check_common(H, W, S, K, h, profile, order, sigma);
     if (rc != SNLM_OK)
         return rc;
-    if (!valid_dtype(dtype) || pitch < W)
+    if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31))
         return SNLM_ERR_ARG;
     if (!is_device_ptr(img) || !is_device_ptr(out))
         return SNLM_ERR_ARG;
@@ -485,7 +486,7 @@ int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, 
     int rc = check_common(H, W, S, K, h, profile, order, sigma);
     if (rc != SNLM_OK)
         return rc;
-    if (!valid_dtype(dtype) || pitch < W || !img_host || !out_host)
+    if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31) || !img_host || !out_host)
         return SNLM_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t in_bytes = (size_t)H * pitch * dtype_size(dtype);
@@ -523,6 +524,12 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
         return SNLM_ERR_ARG;
     if ((delta_in && !is_device_ptr(delta_in)) || (delta_out && !is_device_ptr(delta_out)))
         return SNLM_ERR_ARG;
+    // strides are positive and every element offset fits in 31 bits
+    if (line_step < 1 || elem_step < 1 || out_line_step < 1 || out_elem_step < 1)
+        return SNLM_ERR_ARG;
+    if ((n_lines - 1) * line_step + (long long)(N - 1) * elem_step >= (1LL << 31) ||
+        (n_lines - 1) * out_line_step + (long long)(N - 1) * out_elem_step >= (1LL << 31))
+        return SNLM_ERR_ARG;
     const bool sure = delta_out != nullptr;
     if (sure) {
         const double h2 = (double)h * h;
@@ -545,14 +552,17 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
     a.delta_out = delta_out;
     a.aux_f = Lines{nullptr, DT_F32, 0, 0};
     a.aux_rc = Lines{nullptr, DT_F32, 0, 0};
-    TraceScope ts(SNLM_K_LINE_PASS, static_cast<cudaStream_t>(stream));
-    return status_of(dispatch_pass(K, a, dist_mode_for(dtype, profile), sure, static_cast<cudaStream_t>(stream)));
+    const int dm = dist_mode_for(dtype, profile);
+    TraceScope ts(SNLM_K_LINE_PASS | (dm << 8), static_cast<cudaStream_t>(stream));
+    return status_of(dispatch_pass(K, a, dm, sure, static_cast<cudaStream_t>(stream)));
 }
 
 int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride, int S, int K,
                        int profile, float beta, void *out, void *stream)
 {
     if (n_lines < 1 || N < 1 || stride < N || S < 0 || S > kMaxS || K < 0)
+        return SNLM_ERR_ARG;
+    if ((long long)n_lines * stride >= (1LL << 31))
         return SNLM_ERR_ARG;
     if ((long long)n_lines * N * (2LL * S + 1) >= (1LL << 40))
         return SNLM_ERR_ARG;
@@ -571,8 +581,9 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
     fill_profile(a.g, K, profile, beta_or_default(beta, K));
     a.out = out;
     a.int_out = (dtype == SNLM_U8 && profile == SNLM_BOX) ? 1 : 0;
-    TraceScope ts(SNLM_K_PATCH_DIST, static_cast<cudaStream_t>(stream));
-    return status_of(dispatch_dist(K, a, dist_mode_for(dtype, profile), static_cast<cudaStream_t>(stream)));
+    const int dm = dist_mode_for(dtype, profile);
+    TraceScope ts(SNLM_K_PATCH_DIST | (dm << 8), static_cast<cudaStream_t>(stream));
+    return status_of(dispatch_dist(K, a, dm, static_cast<cudaStream_t>(stream)));
 }
 
 int snlm_trace_enable(int enable)
@@ -613,18 +624,23 @@ int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records)
 
 const char *snlm_kernel_name(int kind)
 {
-    switch (kind) {
-    case SNLM_K_ROW_PASS: return "row_pass";
-    case SNLM_K_COL_PASS: return "col_pass";
-    case SNLM_K_ROW_PASS_SURE: return "row_pass_sure";
-    case SNLM_K_COL_PASS_SURE: return "col_pass_sure";
-    case SNLM_K_SURE_SOLVE: return "sure_solve";
-    case SNLM_K_COMBINE: return "combine";
-    case SNLM_K_SET_THETA: return "set_theta";
-    case SNLM_K_PATCH_DIST: return "patch_dist";
-    case SNLM_K_LINE_PASS: return "line_pass";
-    default: return "unknown";
-    }
+    // low byte: snlm_kernel_kind; bits 8..: how the patch distances were reduced
+    static const char *names[9][4] = {
+        {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
+        {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
+        {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
+        {"col_pass_sure", "col_pass_sure/slide", "col_pass_sure/block", "col_pass_sure/fir"},
+        {"sure_solve", "sure_solve", "sure_solve", "sure_solve"},
+        {"combine", "combine", "combine", "combine"},
+        {"set_theta", "set_theta", "set_theta", "set_theta"},
+        {"patch_dist", "patch_dist/slide", "patch_dist/block", "patch_dist/fir"},
+        {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir"},
+    };
+    const int base = kind & 0xff, dm = kind >> 8;
+    if (base < 0 || base > 8 || dm < 0 || dm > 2)
+        return "unknown";
+    const bool has_dm = base <= 3 || base >= 7;
+    return names[base][has_dm ? dm + 1 : 0];
 }
 
 }  // extern "C"

@@ -9,7 +9,6 @@ namespace snlm {
 constexpr int kMaxK = 7;           // largest patch half-width compiled
 constexpr int kMaxS = 128;         // largest search half-width accepted
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
-constexpr int kChunk = 8;          // search offsets processed per register chunk (SC)
 constexpr int kWarpsPerCta = 8;    // lines per CTA (one warp per line tile)
 constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
 
@@ -57,33 +56,32 @@ struct DistArgs {
 };
 
 // Per-warp shared-memory layout of the pass and distance kernels (in floats).
+// Every array indexed by position uses pad_index: one pad word after every kRun
+// words, so the 32 lanes (which own runs of kRun consecutive positions) hit 32
+// distinct banks.
 struct WarpLayout {
-    int LF;        // line samples
-    int LA;        // one mirror accumulator array (padded)
-    int kinds;     // number of mirror accumulator arrays
-    int LW;        // one stored-weight row (SURE)
+    int LF;        // line samples (padded)
+    int LW;        // one stored-weight row (SURE, padded)
+    int LT;        // one tile-sized row (SURE delta in / out, padded)
     int per_warp;  // total, multiple of 4
 };
 
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
 
-// Accumulator index of relative position p: one pad word after every kRun words
-// so that lanes owning consecutive runs hit distinct banks.
-__host__ __device__ inline int acc_index(int p) { return p + p / kRun; }
+__host__ __device__ inline int pad_index(int p) { return p + p / kRun; }
 
 __host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool dist_only)
 {
     WarpLayout L;
-    const int nch = div_up(S, kChunk);
-    L.LF = 32 * kRun + nch * kChunk + 2 * K + kChunk + 4;
-    L.LF = (L.LF + 3) & ~3;
-    L.LA = dist_only ? 0 : acc_index(32 * kRun + nch * kChunk + kChunk) + 1;
-    L.LA = (L.LA + 3) & ~3;
-    L.kinds = dist_only ? 0 : (sure ? 3 : 2);
-    L.LW = 32 * kRun;
-    int n = L.LF + L.kinds * L.LA;
+    const int nch = div_up(S, kRun);
+    // samples at positions b0 - K + q for q < 32*kRun + nch*kRun + 2K + kRun
+    const int nf = 32 * kRun + nch * kRun + 2 * K + kRun;
+    L.LF = (pad_index(nf) + 4) & ~3;
+    L.LW = (pad_index(32 * kRun) + 4) & ~3;
+    L.LT = L.LW;
+    int n = L.LF;
     if (sure && !dist_only)
-        n += K * L.LW + 2 * 32 * kRun;   // stored weights for |s| <= K, delta in, delta out
+        n += K * L.LW + 2 * L.LT;   // stored weights for |s| <= K, delta in, delta out
     L.per_warp = (n + 3) & ~3;
     return L;
 }

@@ -3,19 +3,22 @@
 //
 // Work decomposition. A CTA holds kWarpsPerCta consecutive lines (rows for a row
 // pass, columns for a column pass) and one tile of T output positions along
-// them; each warp owns one line. Lane r owns the kRun consecutive positions
-// b0 + r*kRun .. b0 + r*kRun + kRun - 1 of the tile's window, where the first
-// HR = ceil(S / kRun) lanes sit left of the tile: they compute only the pairs
-// whose right end falls in the tile.
+// them; each warp owns one line. Lane r owns the M = kRun consecutive positions
+// x0(r) = b0 + r*M .. x0(r) + M - 1 of the tile's window, where the first
+// HR = ceil(S / M) lanes sit left of the tile and only contribute the pairs whose
+// right end falls in the tile.
 //
-// For every search offset s = 1..S the lane lifts its run into the differences
-// Delta_s(x) = f(x+s) - f(x) (Sec. II-A, Eqs. (5)-(7) in difference form), reduces
-// them to patch distances d^2(x, x+s) (Eq. (3)) without a per-pair K-loop for the
-// box profile, and forms w = exp(-d^2/h^2) once per unordered pair: the band
-// symmetry of Eq. (8) gives w(x+s, -s) = w(x, s). The forward contribution goes to
-// the lane's own accumulators, the mirrored one (to pixel x+s) into a small
-// register buffer that is added to per-warp shared-memory accumulators after each
-// chunk of kChunk offsets, in two phases so no two lanes touch the same word.
+// Search offsets are taken in chunks c of M: s = c*M + sg, sg = 1..M. For each s
+// the lane lifts its run into the differences Delta_s(x) = f(x+s) - f(x) (Sec.
+// II-A, Eqs. (5)-(7) in difference form), reduces them to patch distances
+// d^2(x, x+s) of Eq. (3) without a per-pair loop over K for the box profile, and
+// forms w = exp(-d^2/h^2) once per unordered pair: by the band symmetry of Eq. (8),
+// w(x+s, -s) = w(x, s). The forward contribution goes to the lane's own
+// accumulators. The mirrored one (to pixel x+s) lands at register slot m + sg of a
+// 2M-entry buffer whose lower half belongs to lane r + c and upper half to lane
+// r + c + 1, so after the chunk two warp shuffles per slot deliver it; a lane below
+// r + c (or r + c + 1) receives a wrapped value, but such lanes are halo lanes whose
+// own outputs are never stored.
 //
 // Accumulation is centred: A = sum_j w (f(j) - f(i)), Q = sum_j w, so that
 // fhat = f(i) + A/Q; the SURE kernels also keep A2 = sum_j w (f(j) - f(i))^2,
@@ -40,14 +43,19 @@ __device__ __forceinline__ int reflect_index(int x, int n)
     return y < n ? y : p - 1 - y;
 }
 
-__device__ __forceinline__ float load_sample(const Lines &v, long long line, int i)
+__device__ __forceinline__ float load_at(const void *ptr, int dtype, unsigned off)
 {
-    const long long off = line * v.line_step + (long long)i * v.elem_step;
-    if (v.dtype == DT_U8)
-        return (float)__ldg(static_cast<const unsigned char *>(v.ptr) + off);
-    if (v.dtype == DT_F16)
-        return __half2float(__ldg(static_cast<const __half *>(v.ptr) + off));
-    return __ldg(static_cast<const float *>(v.ptr) + off);
+    if (dtype == DT_U8)
+        return (float)__ldg(static_cast<const unsigned char *>(ptr) + off);
+    if (dtype == DT_F16)
+        return __half2float(__ldg(static_cast<const __half *>(ptr) + off));
+    return __ldg(static_cast<const float *>(ptr) + off);
+}
+
+// Element offsets fit in 31 bits (checked by the host before any launch).
+__device__ __forceinline__ float load_sample(const Lines &v, int line, int i)
+{
+    return load_at(v.ptr, v.dtype, (unsigned)(line * (int)v.line_step + i * (int)v.elem_step));
 }
 
 // 2^x with the SFU (MUFU.EX2), flushing denormal results to zero.
@@ -123,39 +131,78 @@ __device__ __forceinline__ void patch_distances(const float (&dl)[M + 2 * K], fl
 }
 
 // Cooperative load of the CTA's line windows into shared memory:
-// buf(w)[q] = sample at position pos0 + q of line line0 + w (reflected), q < len.
-// Row-like views (elem_step == 1) are read along the line; column-like views are
-// read across lines so consecutive threads touch consecutive addresses.
+// buf(w)[pad_index(q)] = sample at position pos0 + q of line line0 + w
+// (reflected), q < len. Row-like views (elem_step == 1) are read along the line;
+// column-like views across lines, so consecutive threads touch consecutive
+// addresses.
 __device__ __forceinline__ void load_windows(float *smem, int per_warp, const Lines &v, int n_lines,
                                              int N, int line0, int pos0, int len)
 {
     if (v.elem_step == 1) {
+        // one warp per line, consecutive lanes on consecutive samples
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int ln = line0 + w;
         float *buf = smem + w * per_warp;
-        for (int q = lane; q < len; q += 32)
-            buf[q] = ln < n_lines ? load_sample(v, ln, reflect_index(pos0 + q, N)) : 0.f;
-    } else {
-        const int total = kWarpsPerCta * len;
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            const int q = e / kWarpsPerCta, w = e % kWarpsPerCta;
-            const int ln = line0 + w;
-            smem[w * per_warp + q] = ln < n_lines ? load_sample(v, ln, reflect_index(pos0 + q, N)) : 0.f;
+        if (ln >= n_lines)
+            return;
+        const unsigned base = (unsigned)(ln * (int)v.line_step);
+        for (int q = lane; q < len; q += 32) {
+            const int x = pos0 + q;
+            const int i = (x >= 0 && x < N) ? x : reflect_index(x, N);
+            buf[q + (q >> 3)] = load_at(v.ptr, v.dtype, base + (unsigned)i);
         }
+    } else {
+        // columns: consecutive threads on consecutive lines of the same position
+        const int w = threadIdx.x % kWarpsPerCta;
+        const int ln = line0 + w;
+        if (ln >= n_lines)
+            return;
+        float *buf = smem + w * per_warp;
+        const int es = (int)v.elem_step;
+        const unsigned base = (unsigned)(ln * (int)v.line_step);
+        for (int q = threadIdx.x / kWarpsPerCta; q < len; q += blockDim.x / kWarpsPerCta) {
+            const int x = pos0 + q;
+            const int i = (x >= 0 && x < N) ? x : reflect_index(x, N);
+            buf[q + (q >> 3)] = load_at(v.ptr, v.dtype, base + (unsigned)(i * es));
+        }
+    }
+}
+
+// Cooperative load of a float image restricted to the tile (positions xa + q,
+// q < T), padded like the windows; `fill` where the position is past the line.
+__device__ __forceinline__ void load_tile(float *smem, int per_warp, int off, const float *img,
+                                          long long line_step, long long elem_step, int n_lines, int N,
+                                          int line0, int xa, int T, float fill)
+{
+    if (elem_step == 1) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int ln = line0 + w;
+        float *buf = smem + w * per_warp + off;
+        const float *row = img + (ln < n_lines ? ln * (int)line_step : 0);
+        for (int q = lane; q < T; q += 32)
+            buf[q + (q >> 3)] = (ln < n_lines && xa + q < N) ? __ldg(row + xa + q) : fill;
+    } else {
+        const int w = threadIdx.x % kWarpsPerCta;
+        const int ln = line0 + w;
+        float *buf = smem + w * per_warp + off;
+        const int es = (int)elem_step;
+        const float *col = img + (ln < n_lines ? ln * (int)line_step : 0);
+        for (int q = threadIdx.x / kWarpsPerCta; q < T; q += blockDim.x / kWarpsPerCta)
+            buf[q + (q >> 3)] = (ln < n_lines && xa + q < N) ? __ldg(col + (xa + q) * es) : fill;
     }
 }
 
 template <int K, int DM, bool SURE>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __grid_constant__ PassArgs p)
 {
-    constexpr int M = kRun, SC = kChunk;
-    constexpr int NF = M + 2 * K;    // lifted positions per run (patch halo K each side)
-    constexpr int NG = NF + SC;      // shifted samples needed for one chunk of offsets
+    constexpr int M = kRun;
+    constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
+    constexpr int NG = 2 * M + 2 * K;    // shifted samples needed for one chunk of M offsets
     extern __shared__ __align__(16) float smem[];
 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.S, N = p.N;
-    const int HR = div_up(S, M), nch = div_up(S, SC);
+    const int HR = div_up(S, M), nch = div_up(S, M);
     const int T = tile_positions(S);
     const int tiles = div_up(N, T);                // grid is linear: tile fastest
     const int xa = (int)(blockIdx.x % tiles) * T;
@@ -164,63 +211,50 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
     const int line = line0 + wid;
     const WarpLayout L = warp_layout(S, K, SURE, false);
 
-    float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q
-    float *const accA = fl + L.LF;
-    float *const accQ = accA + L.LA;
-    float *const accA2 = accQ + L.LA;              // SURE only
-    float *const wK = fl + L.LF + L.kinds * L.LA;  // SURE: w(x, s) for s = 1..K
+    float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
+    float *const wK = fl + L.LF;                   // SURE: w(x, s) for s = 1..K (padded rows)
     float *const din = wK + K * L.LW;              // SURE: delta_in of the tile
-    float *const dst_d = din + 32 * M;             // SURE: delta_out of the tile
+    float *const dst_d = din + L.LT;               // SURE: delta_out of the tile
 
-    // ---- load: the line windows (with reflection), zeroed accumulators, delta_in
-    load_windows(smem, L.per_warp, p.src, p.n_lines, N, line0, b0 - K, L.LF);
-    for (int q = lane; q < L.kinds * L.LA; q += 32)
-        accA[q] = 0.f;
+    // ---- load: the line windows (with reflection) and delta_in
+    load_windows(smem, L.per_warp, p.src, p.n_lines, N, line0, b0 - K, 32 * M + nch * M + 2 * K + M);
     if constexpr (SURE) {
-        if (p.delta_in) {
-            const Lines dv{p.delta_in, DT_F32, p.out_line_step, p.out_elem_step};
-            // positions past the end of the line are never stored; clamp the read
-            if (dv.elem_step == 1) {
-                for (int q = lane; q < T; q += 32)
-                    din[q] = (line < p.n_lines && xa + q < N) ? load_sample(dv, line, xa + q) : 1.f;
-            } else {
-                for (int e = threadIdx.x; e < kWarpsPerCta * T; e += blockDim.x) {
-                    const int q = e / kWarpsPerCta, w = e % kWarpsPerCta;
-                    const int ln = line0 + w;
-                    smem[w * L.per_warp + (din - fl) + q] =
-                        (ln < p.n_lines && xa + q < N) ? load_sample(dv, ln, xa + q) : 1.f;
-                }
-            }
-        } else {
+        if (p.delta_in)
+            load_tile(smem, L.per_warp, (int)(din - fl), p.delta_in, p.out_line_step, p.out_elem_step,
+                      p.n_lines, N, line0, xa, T, 1.f);
+        else
             for (int q = lane; q < T; q += 32)
-                din[q] = 1.f;
-        }
+                din[pad_index(q)] = 1.f;
     }
     __syncthreads();
 
     if (line < p.n_lines) {
+        // samples of the own run with the patch halo: positions x0 - K + u
         float fo[NF];
 #pragma unroll
         for (int u = 0; u < NF; ++u)
-            fo[u] = fl[lane * M + u];
+            fo[u] = fl[9 * lane + u + u / 8];
         float A[M], Q[M], A2[M];
 #pragma unroll
         for (int m = 0; m < M; ++m)
             A[m] = Q[m] = A2[m] = 0.f;
 
         for (int c = 0; c < nch; ++c) {
+            // samples at positions x0 + c*M + 1 - K + j (lanes r + c and r + c + 1)
             float g[NG];
-            const float *gp = fl + lane * M + c * SC + 1;
+            const float *gp = fl + 9 * (lane + c);
 #pragma unroll
             for (int j = 0; j < NG; ++j)
-                g[j] = gp[j];
-            float BA[M + SC], BQ[M + SC], BA2[M + SC];
+                g[j] = gp[(1 + j) + (1 + j) / 8];
+            // mirrored contributions: slot t goes to lane r + c (t < M) or r + c + 1
+            float BA[2 * M], BQ[2 * M], BA2[2 * M];
 #pragma unroll
-            for (int j = 0; j < M + SC; ++j)
-                BA[j] = BQ[j] = BA2[j] = 0.f;
+            for (int t = M + 1; t < 2 * M; ++t)
+                BA[t] = BQ[t] = BA2[t] = 0.f;
+            BA[0] = BQ[0] = BA2[0] = 0.f;
 #pragma unroll
-            for (int sg = 1; sg <= SC; ++sg) {
-                if (c * SC + sg > S)
+            for (int sg = 1; sg <= M; ++sg) {
+                if (c * M + sg > S)
                     break;
                 float dl[NF];
 #pragma unroll
@@ -232,71 +266,74 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
                 for (int m = 0; m < M; ++m) {
                     const float w = exp2_sfu(D[m] * p.c2);
                     const float d = dl[m + K];
+                    const int t = m + sg;
+                    const bool first = (sg == 1);   // slots 1..M are first written at sg = 1
+                    A[m] = fmaf(w, d, A[m]);
+                    BA[t] = first ? -w * d : fmaf(-w, d, BA[t]);
                     if constexpr (SURE) {
                         const float v = w * d;
-                        A[m] += v;
-                        BA[m + sg] -= v;
                         A2[m] = fmaf(v, d, A2[m]);
-                        BA2[m + sg] = fmaf(v, d, BA2[m + sg]);
+                        BA2[t] = first ? v * d : fmaf(v, d, BA2[t]);
                         if (c == 0 && sg <= K)
-                            wK[(sg - 1) * L.LW + lane * M + m] = w;
-                    } else {
-                        A[m] = fmaf(w, d, A[m]);
-                        BA[m + sg] = fmaf(-w, d, BA[m + sg]);
+                            wK[(sg - 1) * L.LW + 9 * lane + m] = w;
                     }
                     Q[m] += w;
-                    BQ[m + sg] += w;
+                    BQ[t] = first ? w : BQ[t] + w;
                 }
             }
-            // add the mirrored contributions: targets lane*M + c*SC + j, j = 1..M+SC-1
-            __syncwarp();
+            // deliver the mirrored contributions
 #pragma unroll
-            for (int j = 1; j <= M; ++j) {
-                const int q = acc_index(lane * M + c * SC + j);
-                accA[q] += BA[j];
-                accQ[q] += BQ[j];
-                if constexpr (SURE)
-                    accA2[q] += BA2[j];
+            for (int j = 0; j < M; ++j) {
+                const float ra = __shfl_up_sync(0xffffffffu, BA[M + j], c + 1);
+                const float rq = __shfl_up_sync(0xffffffffu, BQ[M + j], c + 1);
+                if (j > 0) {
+                    A[j] += __shfl_up_sync(0xffffffffu, BA[j], c) + ra;
+                    Q[j] += __shfl_up_sync(0xffffffffu, BQ[j], c) + rq;
+                } else {
+                    A[j] += ra;
+                    Q[j] += rq;
+                }
+                if constexpr (SURE) {
+                    const float r2 = __shfl_up_sync(0xffffffffu, BA2[M + j], c + 1);
+                    A2[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BA2[j], c) + r2 : r2;
+                }
             }
-            __syncwarp();
-#pragma unroll
-            for (int j = M + 1; j < M + SC; ++j) {
-                const int q = acc_index(lane * M + c * SC + j);
-                accA[q] += BA[j];
-                accQ[q] += BQ[j];
-                if constexpr (SURE)
-                    accA2[q] += BA2[j];
-            }
-            __syncwarp();
         }
+        __syncwarp();
 
         // ---- finalise own pixels: fhat = f + A/Q (and the chained derivative)
         if (lane >= HR) {
 #pragma unroll
             for (int m = 0; m < M; ++m) {
-                const int pr = lane * M + m;
-                const int q = acc_index(pr);
-                const float At = A[m] + accA[q];
-                const float Qt = 1.f + Q[m] + accQ[q];
-                const float mu = __fdiv_rn(At, Qt);
-                fl[pr - HR * M] = fo[m + K] + mu;
+                const int q = 9 * (lane - HR) + m;          // padded tile index
+                const float Qt = 1.f + Q[m];
+                const float mu = __fdiv_rn(A[m], Qt);
+                fl[q] = fo[m + K] + mu;
                 if constexpr (SURE) {
-                    // Eq. (24): the patch-overlap term over 0 < |s| <= min(K, S)
-                    float Tt = 0.f;
+                    // Eq. (24): the patch-overlap term over 0 < |s| <= min(K, S),
+                    // T = sum_s g(s) [wf (a_s - mu) a_-s + wb (a_-s - mu) a_s] = TA - mu TB
+                    // with a_s = f(x+s) - f(x), wf = w(x, s), wb = w(x-s, s).
+                    float TA = 0.f, TB = 0.f;
 #pragma unroll
                     for (int sg = 1; sg <= K; ++sg) {
                         if (sg > S)
                             break;
                         const float ap = fo[m + K + sg] - fo[m + K];
                         const float am = fo[m + K - sg] - fo[m + K];
-                        const float wf = wK[(sg - 1) * L.LW + pr];
-                        const float wb = wK[(sg - 1) * L.LW + pr - sg];
-                        const float t = wf * (ap - mu) * am + wb * (am - mu) * ap;
-                        Tt = (DM == DIST_FIR) ? fmaf(p.g[K + sg], t, Tt) : Tt + t;
+                        float wf = wK[(sg - 1) * L.LW + 9 * lane + m];
+                        const int pb = 8 * lane + m - sg;   // position of x - s, >= 0
+                        float wb = wK[(sg - 1) * L.LW + pb + (pb >> 3)];
+                        if constexpr (DM == DIST_FIR) {
+                            wf *= p.g[K + sg];
+                            wb *= p.g[K + sg];
+                        }
+                        TA = fmaf(wf + wb, ap * am, TA);
+                        TB = fmaf(wf, am, fmaf(wb, ap, TB));
                     }
-                    const float var = (A2[m] + accA2[q]) - mu * At;   // sum_j w (f(j) - fhat)^2
+                    const float Tt = fmaf(-mu, TB, TA);
+                    const float var = A2[m] - mu * A[m];   // sum_j w (f(j) - fhat)^2
                     const float num = p.h2 + 2.f * Tt + 2.f * var;
-                    dst_d[pr - HR * M] = din[pr - HR * M] * __fdiv_rn(num, Qt * p.h2);
+                    dst_d[q] = din[q] * __fdiv_rn(num, Qt * p.h2);
                 }
             }
         }
@@ -305,66 +342,65 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
 
     // ---- store: fhat (optionally blended), delta_out, partial sums
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const bool row_like = p.out_elem_step == 1;
-    const int total = kWarpsPerCta * T;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int q, w;
-        if (row_like) {
-            w = e / T;
-            q = e - w * T;
-        } else {
-            q = e / kWarpsPerCta;
-            w = e % kWarpsPerCta;
-        }
-        const int ln = line0 + w, x = xa + q;
-        if (ln >= p.n_lines || x >= N)
-            continue;
+    {
+        const bool row_like = p.out_elem_step == 1;
+        const int w = row_like ? wid : (int)(threadIdx.x % kWarpsPerCta);
+        const int q0 = row_like ? lane : (int)(threadIdx.x / kWarpsPerCta);
+        const int qs = row_like ? 32 : (int)(blockDim.x / kWarpsPerCta);
+        const int ln = line0 + w;
         const float *wb = smem + w * L.per_warp;
-        const long long o = ln * p.out_line_step + (long long)x * p.out_elem_step;
-        float v = wb[q];
-        if (p.blend)
-            v = 0.5f * (v + p.blend[o]);
-        p.dst[o] = v;
-        if constexpr (SURE) {
-            const float dv = wb[(dst_d - fl) + q];
-            if (p.delta_out)
-                p.delta_out[o] = dv;
-            s[5] += dv;
-            if (p.aux_rc.ptr) {
-                // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
-                const float rc = load_sample(p.aux_rc, ln, x);
-                const float fv = load_sample(p.aux_f, ln, x);
-                const float mm = 0.5f * (rc + v), dd = 0.5f * (rc - v);
-                s[0] = fmaf(mm, mm, s[0]);
-                s[1] = fmaf(mm, dd, s[1]);
-                s[2] = fmaf(dd, dd, s[2]);
-                s[3] = fmaf(fv, mm, s[3]);
-                s[4] = fmaf(fv, dd, s[4]);
+        const int qe = (ln < p.n_lines) ? min(T, N - xa) : 0;
+        const int ls = (int)p.out_line_step, es = (int)p.out_elem_step;
+        for (int q = q0; q < qe; q += qs) {
+            const int x = xa + q;
+            const unsigned o = (unsigned)(ln * ls + x * es);
+            float v = wb[q + (q >> 3)];
+            if (p.blend)
+                v = 0.5f * (v + __ldg(p.blend + o));
+            p.dst[o] = v;
+            if constexpr (SURE) {
+                const float dv = wb[(int)(dst_d - fl) + q + (q >> 3)];
+                if (p.delta_out)
+                    p.delta_out[o] = dv;
+                s[5] += dv;
+                if (p.aux_rc.ptr) {
+                    // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
+                    const float rc = load_sample(p.aux_rc, ln, x);
+                    const float fv = load_sample(p.aux_f, ln, x);
+                    const float mm = 0.5f * (rc + v), dd = 0.5f * (rc - v);
+                    s[0] = fmaf(mm, mm, s[0]);
+                    s[1] = fmaf(mm, dd, s[1]);
+                    s[2] = fmaf(dd, dd, s[2]);
+                    s[3] = fmaf(fv, mm, s[3]);
+                    s[4] = fmaf(fv, dd, s[4]);
+                }
             }
         }
     }
     if constexpr (SURE) {
         if (p.partials) {
-            // deterministic reduction: fp64 warp tree, then warps in order
-            double d[6];
+            // deterministic reduction: float warp tree, then the warps in order in fp64
+            const int nk = p.aux_rc.ptr ? 6 : 1;
+            __shared__ float red[kWarpsPerCta][6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                d[k] = s[k];
+                if (k >= 6 - nk) {
+                    float v = s[k];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+                    for (int o = 16; o > 0; o >>= 1)
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0)
+                        red[wid][k] = v;
+                } else if (lane == 0) {
+                    red[wid][k] = 0.f;
+                }
             }
-            __shared__ double red[kWarpsPerCta][6];
-            if (lane == 0)
-#pragma unroll
-                for (int k = 0; k < 6; ++k)
-                    red[wid][k] = d[k];
             __syncthreads();
             if (threadIdx.x < kPartials) {
                 double t = 0.0;
                 if (threadIdx.x < 6)
                     for (int w = 0; w < kWarpsPerCta; ++w)
-                        t += red[w][threadIdx.x];
+                        t += (double)red[w][threadIdx.x];
                 p.partials[(long long)blockIdx.x * kPartials + threadIdx.x] = t;
             }
         }
@@ -376,15 +412,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
 template <int K, int DM>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) patch_dist_kernel(const __grid_constant__ DistArgs p)
 {
-    constexpr int M = kRun, SC = kChunk;
+    constexpr int M = kRun;
     constexpr int NF = M + 2 * K;
-    constexpr int NG = NF + SC;
+    constexpr int NG = 2 * M + 2 * K;
     extern __shared__ __align__(16) float smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.S, N = p.N;
-    const int HR = div_up(S, M), nch = div_up(S, SC);
+    const int HR = div_up(S, M), nch = div_up(S, M);
     const int T = tile_positions(S);
-    const int tiles = div_up(N, T);                // grid is linear: tile fastest
+    const int tiles = div_up(N, T);
     const int xa = (int)(blockIdx.x % tiles) * T;
     const int b0 = xa - HR * M;
     const int line0 = (int)(blockIdx.x / tiles) * kWarpsPerCta;
@@ -392,7 +428,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) patch_dist_kernel(const 
     const WarpLayout L = warp_layout(S, K, false, true);
     float *const fl = smem + wid * L.per_warp;
 
-    load_windows(smem, L.per_warp, p.src, p.n_lines, N, line0, b0 - K, L.LF);
+    load_windows(smem, L.per_warp, p.src, p.n_lines, N, line0, b0 - K, 32 * M + nch * M + 2 * K + M);
     __syncthreads();
     if (line >= p.n_lines)
         return;
@@ -417,16 +453,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) patch_dist_kernel(const 
     float fo[NF];
 #pragma unroll
     for (int u = 0; u < NF; ++u)
-        fo[u] = fl[lane * M + u];
+        fo[u] = fl[9 * lane + u + u / 8];
     for (int c = 0; c < nch; ++c) {
         float g[NG];
-        const float *gp = fl + lane * M + c * SC + 1;
+        const float *gp = fl + 9 * (lane + c);
 #pragma unroll
         for (int j = 0; j < NG; ++j)
-            g[j] = gp[j];
+            g[j] = gp[(1 + j) + (1 + j) / 8];
 #pragma unroll
-        for (int sg = 1; sg <= SC; ++sg) {
-            const int s = c * SC + sg;
+        for (int sg = 1; sg <= M; ++sg) {
+            const int s = c * M + sg;
             if (s > S)
                 break;
             float dl[NF];
