@@ -146,6 +146,29 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
 
 
 /*
+ * Separable NLM without any device allocation (no counterpart in the paper).
+ * Same computation, arguments and results as snlm_denoise, for callers that may
+ * not call cudaMalloc or cudaFree at run time: real-time loops (an allocation can
+ * synchronise the device and take an unbounded time), plug-ins whose host
+ * application owns all device memory, programs that must keep a fixed footprint.
+ * The caller passes the input and output buffers; the intermediate images use a
+ * fixed scratch area of SNLM_NOALLOC_SCRATCH_BYTES compiled into the library
+ * (held by every device that loads the library until the process exits).
+ *  - Images that need more scratch are rejected with SNLM_ERR_ARG before any work
+ *    is queued; snlm_workspace_bytes(H, W, order) <= SNLM_NOALLOC_SCRATCH_BYTES is
+ *    a sufficient condition (e.g. SURE up to about 1400 x 1400, RC up to about
+ *    2800 x 2800).
+ *  - The first call on a device looks up the scratch area's device address; make
+ *    that first call before capturing any stream.
+ *  - All calls in the process share the scratch area. Calls whose device work can
+ *    overlap in time (several streams, or several host threads without ordering)
+ *    race on it and corrupt each other's results: serialise them.
+ */
+#define SNLM_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int snlm_denoise_noalloc(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                         int profile, int order, float sigma, float beta, float *out, void *stream);
+
+/*
  * Launch tracing (no counterpart in the paper; for profiling). When enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded on
  * the launching stream, and snlm_trace_read returns one record per launch:

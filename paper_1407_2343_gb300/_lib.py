@@ -56,6 +56,8 @@ def load(build_if_missing: bool = False):
         lib.snlm_nlm_1d.restype = ci
         lib.snlm_patch_dist_1d.argtypes = [vp, ci, ci, ci, ci, ci, ci, ci, cf, vp, vp]
         lib.snlm_patch_dist_1d.restype = ci
+        lib.snlm_denoise_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, ci, cf, cf, vp, vp]
+        lib.snlm_denoise_noalloc.restype = ci
         lib.snlm_trace_enable.argtypes = [ci]
         lib.snlm_trace_enable.restype = ci
         lib.snlm_trace_read.argtypes = [ctypes.POINTER(ci), fp, ci, ctypes.POINTER(ci)]
@@ -71,5 +73,5 @@ def load(build_if_missing: bool = False):
 EXPORTED = [
     "snlm_status_str", "snlm_version", "snlm_default_h", "snlm_workspace_bytes", "snlm_denoise",
     "snlm_denoise_ws", "snlm_denoise_host", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
-    "snlm_trace_read", "snlm_kernel_name",
+    "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc",
 ]

@@ -216,3 +216,25 @@ def snlm_trace_read(max_records: int = 1 << 16):
 
 def snlm_kernel_name(kind: int) -> str:
     return _lib.load().snlm_kernel_name(int(kind)).decode()
+
+
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def snlm_denoise_noalloc(img, S: int, K: int, h: float | None = None, profile="box", order="RC",
+                         sigma: float | None = None, beta: float = 0.0, out=None, stream=None):
+    """snlm_denoise without any device allocation inside the library: the
+    intermediate images use a fixed 32 MiB scratch area compiled into it. For
+    callers that may not allocate device memory at run time; `out` should then be
+    given (a new output tensor is allocated here only if it is not). Calls that can
+    overlap on the GPU share the scratch area and must be serialised."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    h = _h_for(h, sigma, K, profile, beta)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    rc = _lib.load().snlm_denoise_noalloc(_ptr(img), dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                          _order(order), float(sigma or 0.0), float(beta or 0.0), _ptr(out),
+                                          _stream_ptr(stream))
+    _check(rc, "snlm_denoise_noalloc")
+    return out
