@@ -100,7 +100,7 @@ long long pass_ctas(int n_lines, int N, int S)
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-    size_t tmp, frc, delta, part_rc, part_cr, info, total;
+    size_t tmp, frc, delta, part_rc, part_cr, solve, info, total;
     long long n_part_rc, n_part_cr;
 };
 
@@ -130,6 +130,9 @@ WsLayout ws_layout(int H, int W, int S, int order)
     L.part_cr = off;
     if (order == SNLM_SURE)
         off += align_up((size_t)L.n_part_cr * kPartials * sizeof(double), 256);
+    L.solve = off;
+    if (order == SNLM_SURE)
+        off += align_up((size_t)2 * kSolveScratchRecords * kPartials * sizeof(double), 256);
     L.info = off;
     off += 256;
     L.total = off;
@@ -331,8 +334,8 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
     double *part_rc = reinterpret_cast<double *>(base + L.part_rc);
     double *part_cr = reinterpret_cast<double *>(base + L.part_cr);
     double *winfo = reinterpret_cast<double *>(base + L.info);
+    double *wsolve = reinterpret_cast<double *>(base + L.solve);
     const double bt = beta_or_default(beta, K);
-    const bool sure = order == SNLM_SURE;
     cudaError_t e = cudaSuccess;
 #define SNLM_TRY(x)            \
     do {                       \
@@ -390,7 +393,7 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         {
             TraceScope ts(SNLM_K_SURE_SOLVE, st);
             SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
-                                       (double)sigma * sigma, winfo, st));
+                                       (double)sigma * sigma, winfo, wsolve, st));
         }
         {
             TraceScope ts(SNLM_K_COMBINE, st);

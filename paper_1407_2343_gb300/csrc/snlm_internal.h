@@ -9,7 +9,7 @@ namespace snlm {
 constexpr int kMaxK = 7;           // largest patch half-width compiled
 constexpr int kMaxS = 128;         // largest search half-width accepted
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
-constexpr int kWarpsPerCta = 8;    // lines per CTA (one warp per line tile)
+constexpr int kWarpsPerCta = 4;    // lines per CTA (one warp per line tile)
 constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
 
 enum DType { DT_U8 = 0, DT_F16 = 1, DT_F32 = 2 };
@@ -96,8 +96,10 @@ __host__ __device__ inline int tile_positions(int S)
 template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
 template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);
 
+// scratch: 2 * kSolveScratchRecords * kPartials doubles
+constexpr int kSolveScratchRecords = 128;
 cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
-                              double sigma2, double *info, cudaStream_t st);
+                              double sigma2, double *info, double *scratch, cudaStream_t st);
 cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info, long long n,
                            cudaStream_t st);
 cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st);

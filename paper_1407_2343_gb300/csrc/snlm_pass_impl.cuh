@@ -193,7 +193,7 @@ __device__ __forceinline__ void load_tile(float *smem, int per_warp, int off, co
 }
 
 template <int K, int DM, bool SURE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __grid_constant__ PassArgs p)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SURE ? 4 : 5) nlm_pass_kernel(const __grid_constant__ PassArgs p)
 {
     constexpr int M = kRun;
     constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 2) nlm_pass_kernel(const __
 // Patch distances only: the same lift and reduction as the pass kernel, written
 // out as d^2(x, x+s) for s in [-S, S] (the mirrored half from the band symmetry).
 template <int K, int DM>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) patch_dist_kernel(const __grid_constant__ DistArgs p)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 4) patch_dist_kernel(const __grid_constant__ DistArgs p)
 {
     constexpr int M = kRun;
     constexpr int NF = M + 2 * K;

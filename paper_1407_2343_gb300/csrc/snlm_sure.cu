@@ -9,6 +9,7 @@ namespace snlm {
 namespace {
 
 constexpr int kSolveThreads = 256;
+constexpr int kSolveBlocks = kSolveScratchRecords;   // first-level slices of the records
 
 // Sum `n` records of kPartials doubles in a fixed order: thread t takes records
 // t, t + 256, ... in sequence, then a fixed binary tree over threads.
@@ -67,6 +68,24 @@ __device__ void solve2_sym(double a, double c, double e, double b0, double b1, d
     const double coef = (v0 * b0 + v1 * b1) / lam;
     *t0 = coef * v0;
     *t1 = coef * v1;
+}
+
+// The SURE objective of Eq. (17) is minimised over f~ = theta1 f_rc + theta2 f_cr
+// (Eq. (14)). It is solved here in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2,
+// f~ = alpha m + beta d, theta1 = (alpha + beta)/2, theta2 = (alpha - beta)/2: the
+// same minimiser (a linear change of variables; det/trace^2 is unchanged), but the
+// sums that fix the nearly singular direction (beta) are made of the small
+// differences d, so float32 per-pixel products keep them accurate.
+// First level: block b sums records [b*per, min(n, (b+1)*per)) in a fixed order.
+__global__ void __launch_bounds__(kSolveThreads) sure_partial_kernel(const double *part, int n, int per,
+                                                                     double *out)
+{
+    __shared__ double sh[kPartials * kSolveThreads];
+    const int lo = blockIdx.x * per, hi = min(n, lo + per);
+    double r[kPartials];
+    reduce_records(part + (long long)lo * kPartials, max(0, hi - lo), sh, r);
+    if (threadIdx.x < kPartials)
+        out[(long long)blockIdx.x * kPartials + threadIdx.x] = r[threadIdx.x];
 }
 
 // The SURE objective of Eq. (17) is minimised over f~ = theta1 f_rc + theta2 f_cr
@@ -143,9 +162,16 @@ __global__ void set_theta_kernel(double *info, double t0, double t1)
 }  // namespace
 
 cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
-                              double sigma2, double *info, cudaStream_t st)
+                              double sigma2, double *info, double *scratch, cudaStream_t st)
 {
-    sure_solve_kernel<<<1, kSolveThreads, 0, st>>>(part_rc, n_rc, part_cr, n_cr, sigma2, info);
+    // two fixed-order levels: kSolveBlocks slices per record set, then one block
+    const int per_rc = (n_rc + kSolveBlocks - 1) / kSolveBlocks;
+    const int per_cr = (n_cr + kSolveBlocks - 1) / kSolveBlocks;
+    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_rc, n_rc, per_rc, scratch);
+    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_cr, n_cr, per_cr,
+                                                                scratch + kSolveBlocks * kPartials);
+    sure_solve_kernel<<<1, kSolveThreads, 0, st>>>(scratch, kSolveBlocks, scratch + kSolveBlocks * kPartials,
+                                                   kSolveBlocks, sigma2, info);
     return cudaGetLastError();
 }
 
