@@ -169,6 +169,64 @@ int snlm_denoise_noalloc(const void *img, int dtype, int H, int W, int pitch, in
                          int profile, int order, float sigma, float beta, float *out, void *stream);
 
 /*
+ * Batched denoising of many independent images (uneven sizes, per-image S, K, h,
+ * profile, order) in persistent launches over a tile work queue.
+ *
+ * A plan turns the requests into jobs (one per 1-D pass of an image, plus the
+ * SURE solve and combination) and jobs into CTA-sized units (4 lines x one tile).
+ * Units are queued by dependency level (all first passes, then all second passes,
+ * ...), and one persistent kernel per patch half-width K pops them with an atomic
+ * counter; a unit whose job depends on unfinished jobs waits on per-job completion
+ * counters. Every wait is bounded (snlm_batch_config.spin_limit_us); when a bound
+ * is hit the kernel records it and stops, and snlm_batch_plan_status returns
+ * SNLM_ERR_TIMEOUT. Each image's result equals snlm_denoise's bit for bit for the
+ * RC, CR and AVG orders (same per-unit code); for SURE the per-image sums are
+ * reduced in a different fixed order, so theta may differ in the last bits.
+ */
+typedef struct {
+    const void *img;   /* DEVICE input, H rows of `pitch` elements of `dtype` */
+    float *out;        /* DEVICE output, H*W float32 */
+    int dtype, H, W, pitch;
+    int S, K;
+    float h;
+    int profile, order;
+    float sigma, beta; /* as in snlm_denoise */
+} snlm_request;
+
+typedef struct {
+    int ctas_per_sm;   /* persistent CTAs per SM; <= 0: as many as fit */
+    int queue_order;   /* 0: as given, 1: largest images first, 2: smallest first */
+    int spin_limit_us; /* bound of one dependency wait; <= 0: 2 000 000 */
+    int fail_job;      /* testing aid: >= 0 makes that job's first dependency
+                          unsatisfiable (host-side fault injection); -1 normally */
+} snlm_batch_config;
+
+typedef struct snlm_batch_plan snlm_batch_plan;
+
+/* Builds a plan (host only). Every request is validated as in snlm_denoise;
+ * K must be >= 1 in a batch. cfg may be NULL (defaults). */
+int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_config *cfg,
+                           snlm_batch_plan **plan);
+/* DEVICE scratch the plan needs (job table, counters, intermediate images). */
+size_t snlm_batch_plan_workspace_bytes(const snlm_batch_plan *plan);
+/* Copies the job table into `workspace` (16-byte aligned, >= the bytes above) on
+ * `stream` and binds the plan to it. */
+int snlm_batch_plan_upload(snlm_batch_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
+/* Queues one run of the whole batch on `stream` (counter reset + one persistent
+ * kernel per K class); replays the captured graph if snlm_batch_plan_capture was
+ * called. */
+int snlm_batch_plan_launch(snlm_batch_plan *plan, void *stream);
+/* Records one run into a CUDA graph (stream capture on `stream`, thread-local
+ * mode) and instantiates it; later launches replay the graph. */
+int snlm_batch_plan_capture(snlm_batch_plan *plan, void *stream);
+/* Waits for `stream`, then reports whether a bounded wait gave up in the last run
+ * (SNLM_ERR_TIMEOUT) and clears the flag. */
+int snlm_batch_plan_status(snlm_batch_plan *plan, void *stream);
+/* Number of jobs, units and K classes of the plan (any pointer may be NULL). */
+int snlm_batch_plan_info(const snlm_batch_plan *plan, int *jobs, int *units, int *classes);
+void snlm_batch_plan_destroy(snlm_batch_plan *plan);
+
+/*
  * Launch tracing (no counterpart in the paper; for profiling). When enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded on
  * the launching stream, and snlm_trace_read returns one record per launch:
@@ -190,7 +248,8 @@ typedef enum {
     SNLM_K_COMBINE = 5,        /* theta1 f_rc + theta2 f_cr (Eq. (14)) */
     SNLM_K_SET_THETA = 6,      /* writes the fixed weights of the RC / CR / AVG orders */
     SNLM_K_PATCH_DIST = 7,     /* patch distances of Eq. (3) */
-    SNLM_K_LINE_PASS = 8       /* snlm_nlm_1d pass over arbitrary strided lines */
+    SNLM_K_LINE_PASS = 8,      /* snlm_nlm_1d pass over arbitrary strided lines */
+    SNLM_K_BATCH = 9           /* one persistent batch kernel (one K class) */
 } snlm_kernel_kind;
 
 int snlm_trace_enable(int enable);

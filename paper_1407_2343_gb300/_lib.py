@@ -21,6 +21,20 @@ class LibraryMissing(RuntimeError):
     pass
 
 
+class Request(ctypes.Structure):
+    """snlm_request of include/snlm.h."""
+    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("S", ctypes.c_int),
+                ("K", ctypes.c_int), ("h", ctypes.c_float), ("profile", ctypes.c_int), ("order", ctypes.c_int),
+                ("sigma", ctypes.c_float), ("beta", ctypes.c_float)]
+
+
+class BatchConfig(ctypes.Structure):
+    """snlm_batch_config of include/snlm.h."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("queue_order", ctypes.c_int),
+                ("spin_limit_us", ctypes.c_int), ("fail_job", ctypes.c_int)]
+
+
 def load(build_if_missing: bool = False):
     """Load libsnlm.so (optionally building it first). Raises LibraryMissing."""
     global _lib
@@ -58,6 +72,23 @@ def load(build_if_missing: bool = False):
         lib.snlm_patch_dist_1d.restype = ci
         lib.snlm_denoise_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, ci, cf, cf, vp, vp]
         lib.snlm_denoise_noalloc.restype = ci
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.snlm_batch_plan_create.argtypes = [ctypes.POINTER(Request), ci, ctypes.POINTER(BatchConfig), pp]
+        lib.snlm_batch_plan_create.restype = ci
+        lib.snlm_batch_plan_workspace_bytes.argtypes = [vp]
+        lib.snlm_batch_plan_workspace_bytes.restype = csz
+        lib.snlm_batch_plan_upload.argtypes = [vp, vp, csz, vp]
+        lib.snlm_batch_plan_upload.restype = ci
+        lib.snlm_batch_plan_launch.argtypes = [vp, vp]
+        lib.snlm_batch_plan_launch.restype = ci
+        lib.snlm_batch_plan_capture.argtypes = [vp, vp]
+        lib.snlm_batch_plan_capture.restype = ci
+        lib.snlm_batch_plan_status.argtypes = [vp, vp]
+        lib.snlm_batch_plan_status.restype = ci
+        lib.snlm_batch_plan_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
+        lib.snlm_batch_plan_info.restype = ci
+        lib.snlm_batch_plan_destroy.argtypes = [vp]
+        lib.snlm_batch_plan_destroy.restype = None
         lib.snlm_trace_enable.argtypes = [ci]
         lib.snlm_trace_enable.restype = ci
         lib.snlm_trace_read.argtypes = [ctypes.POINTER(ci), fp, ci, ctypes.POINTER(ci)]
@@ -73,5 +104,7 @@ def load(build_if_missing: bool = False):
 EXPORTED = [
     "snlm_status_str", "snlm_version", "snlm_default_h", "snlm_workspace_bytes", "snlm_denoise",
     "snlm_denoise_ws", "snlm_denoise_host", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
-    "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc",
+    "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc", "snlm_batch_plan_create",
+    "snlm_batch_plan_workspace_bytes", "snlm_batch_plan_upload", "snlm_batch_plan_launch",
+    "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
 ]

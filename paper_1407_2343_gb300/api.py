@@ -238,3 +238,64 @@ def snlm_denoise_noalloc(img, S: int, K: int, h: float | None = None, profile="b
                                           _stream_ptr(stream))
     _check(rc, "snlm_denoise_noalloc")
     return out
+
+
+# ---------------------------------------------------------------- batches
+
+
+def _request(img, out, S, K, h, profile, order, sigma, beta):
+    dt, H, W, pitch = _image_args(img)
+    return _lib.Request(img.data_ptr(), out.data_ptr(), dt, H, W, pitch, int(S), int(K), float(h),
+                        _profile(profile), _order(order), float(sigma or 0.0), float(beta or 0.0))
+
+
+def snlm_batch_plan_create(requests, ctas_per_sm: int = 0, queue_order: int = 0, spin_limit_us: int = 0,
+                           fail_job: int = -1):
+    """Build a batch plan. `requests` is a list of dicts with keys img, out (CUDA
+    tensors), S, K, h, and optionally profile, order, sigma, beta. Returns an opaque
+    handle (int); keep the tensors alive while the plan is used."""
+    arr = (_lib.Request * len(requests))()
+    for i, r in enumerate(requests):
+        arr[i] = _request(r["img"], r["out"], r["S"], r["K"], r["h"], r.get("profile", "box"),
+                          r.get("order", "RC"), r.get("sigma", 0.0), r.get("beta", 0.0))
+    cfg = _lib.BatchConfig(int(ctas_per_sm), int(queue_order), int(spin_limit_us), int(fail_job))
+    h = ctypes.c_void_p()
+    _check(_lib.load().snlm_batch_plan_create(arr, len(requests), ctypes.byref(cfg), ctypes.byref(h)),
+           "snlm_batch_plan_create")
+    return h.value
+
+
+def snlm_batch_plan_workspace_bytes(plan) -> int:
+    return int(_lib.load().snlm_batch_plan_workspace_bytes(ctypes.c_void_p(plan)))
+
+
+def snlm_batch_plan_upload(plan, workspace, stream=None):
+    _check(_lib.load().snlm_batch_plan_upload(ctypes.c_void_p(plan), _ptr(workspace),
+                                              int(workspace.numel() * workspace.element_size()),
+                                              _stream_ptr(stream)), "snlm_batch_plan_upload")
+
+
+def snlm_batch_plan_launch(plan, stream=None):
+    _check(_lib.load().snlm_batch_plan_launch(ctypes.c_void_p(plan), _stream_ptr(stream)),
+           "snlm_batch_plan_launch")
+
+
+def snlm_batch_plan_capture(plan, stream=None):
+    _check(_lib.load().snlm_batch_plan_capture(ctypes.c_void_p(plan), _stream_ptr(stream)),
+           "snlm_batch_plan_capture")
+
+
+def snlm_batch_plan_status(plan, stream=None) -> int:
+    """0 when the last run finished normally, ERR_TIMEOUT when a bounded wait gave up."""
+    return int(_lib.load().snlm_batch_plan_status(ctypes.c_void_p(plan), _stream_ptr(stream)))
+
+
+def snlm_batch_plan_info(plan):
+    j, u, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.load().snlm_batch_plan_info(ctypes.c_void_p(plan), ctypes.byref(j), ctypes.byref(u),
+                                            ctypes.byref(c)), "snlm_batch_plan_info")
+    return {"jobs": j.value, "units": u.value, "classes": c.value}
+
+
+def snlm_batch_plan_destroy(plan):
+    _lib.load().snlm_batch_plan_destroy(ctypes.c_void_p(plan))

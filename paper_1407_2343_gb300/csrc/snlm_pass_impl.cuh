@@ -192,22 +192,24 @@ __device__ __forceinline__ void load_tile(float *smem, int per_warp, int off, co
     }
 }
 
+// One CTA-sized unit of a pass: kWarpsPerCta lines x one tile of positions.
+// `bid` enumerates the units of the pass (tile fastest). All threads of the CTA
+// must call it (it contains CTA barriers); smem must hold the pass's layout.
 template <int K, int DM, bool SURE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SURE ? 4 : 5) nlm_pass_kernel(const __grid_constant__ PassArgs p)
+__device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *smem)
 {
     constexpr int M = kRun;
     constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
     constexpr int NG = 2 * M + 2 * K;    // shifted samples needed for one chunk of M offsets
-    extern __shared__ __align__(16) float smem[];
 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.S, N = p.N;
     const int HR = div_up(S, M), nch = div_up(S, M);
     const int T = tile_positions(S);
-    const int tiles = div_up(N, T);                // grid is linear: tile fastest
-    const int xa = (int)(blockIdx.x % tiles) * T;
+    const int tiles = div_up(N, T);                // units are numbered tile fastest
+    const int xa = (bid % tiles) * T;
     const int b0 = xa - HR * M;
-    const int line0 = (int)(blockIdx.x / tiles) * kWarpsPerCta;
+    const int line0 = (bid / tiles) * kWarpsPerCta;
     const int line = line0 + wid;
     const WarpLayout L = warp_layout(S, K, SURE, false);
 
@@ -401,10 +403,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SURE ? 4 : 5) nlm_pass_kern
                 if (threadIdx.x < 6)
                     for (int w = 0; w < kWarpsPerCta; ++w)
                         t += (double)red[w][threadIdx.x];
-                p.partials[(long long)blockIdx.x * kPartials + threadIdx.x] = t;
+                p.partials[(long long)bid * kPartials + threadIdx.x] = t;
             }
         }
     }
+}
+
+template <int K, int DM, bool SURE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, SURE ? 4 : 5) nlm_pass_kernel(const __grid_constant__ PassArgs p)
+{
+    extern __shared__ __align__(16) float smem[];
+    process_tile<K, DM, SURE>(p, (int)blockIdx.x, smem);
 }
 
 // Patch distances only: the same lift and reduction as the pass kernel, written
