@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rc", action="store_true", help="skip the extra RC-order measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--batch-images", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -201,6 +205,111 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def measure_batched(a, dev, stream):
+    """The uneven batch: images with sides log-uniform in [64, 1024], aspect in
+    [1/2, 2], u8/f16, sigma ~ U[10, 50], S in {5,10,15}, K in {2,3,5}, box, RC.
+    Plain: one snlm_denoise_ws call per image. Batched: the autotuned persistent
+    launch, replayed from a CUDA graph. Both time whole passes over the batch with
+    CUDA events; inputs resident, outputs preallocated."""
+    import torch
+
+    from paper_1407_2343_gb300 import api, synth
+    from paper_1407_2343_gb300.batch import Batch, autotune
+
+    specs = synth.batch_specs(a.batch_images, seed=0)
+    reqs = []
+    for i, s in enumerate(specs):
+        img = torch.from_numpy(synth.noisy_image(s["H"], s["W"], s["sigma"], seed=1000 + i, dtype=s["dtype"])).to(dev)
+        reqs.append(dict(img=img, out=torch.empty((s["H"], s["W"]), dtype=torch.float32, device=dev),
+                         S=s["S"], K=s["K"], h=api.snlm_default_h(s["sigma"], s["K"]), profile="box",
+                         order="RC", sigma=s["sigma"], beta=0.0))
+    px = sum(s["H"] * s["W"] for s in specs)
+    ws = torch.empty(max(api.snlm_workspace_bytes(s["H"], s["W"], "RC") for s in specs), dtype=torch.uint8, device=dev)
+    plain_out = [torch.empty_like(r["out"]) for r in reqs]
+
+    def plain():
+        for r, o in zip(reqs, plain_out):
+            api.snlm_denoise_ws(r["img"], r["S"], r["K"], r["h"], "box", "RC", r["sigma"], out=o, workspace=ws,
+                                stream=stream)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(20, a.steps // 20))
+    t_plain = timed(plain, reps)
+    cands = [dict(ctas_per_sm=c, queue_order=q) for c in (2, 4, 0) for q in (0, 1)]
+    cfg, table = autotune(reqs, candidates=cands, reps=3)
+    batch = Batch(reqs, **cfg)
+    batch.capture()
+    t_batch = timed(batch.run, reps)
+    status = batch.status()
+    diff = max(float((r["out"] - o).abs().max()) for r, o in zip(reqs, plain_out))
+    info = batch.info()
+    batch.close()
+    n = len(reqs)
+    return {"workload": f"{n} uneven images (sides 64..1024 log-uniform, aspect 1/2..2, u8/f16, "
+                        f"S in {{5,10,15}}, K in {{2,3,5}}, box, RC), {px / 1e6:.2f} Mpixel in total",
+            "plain_images_per_s": n / (t_plain * 1e-3), "batched_images_per_s": n / (t_batch * 1e-3),
+            "plain_ms": t_plain, "batched_ms": t_batch, "speedup": t_plain / t_batch,
+            "max_abs_diff_batched_vs_plain": diff, "status": status, "config": cfg,
+            "autotune_table": table, "plan": info, "reps": reps,
+            "plain_gpu_launches_per_pass": 3 * n, "batched_gpu_launches_per_pass": info["classes"]}
+
+
+def measure_served(a, dev):
+    """Poisson arrivals swept from 0.2x to 1.5x of the plain path's capacity;
+    sizes {128, 512, 1024, 2048, 4096}^2 with weights {.3, .3, .2, .15, .05}; each
+    request with its own S, K, h, profile and order. Continuous batching (Server)
+    against the plain per-request path on the same schedule; latency is arrival to
+    result in host memory. Accuracy: the served results against the plain ones
+    (all requests) and against the FP64 oracle (a sample of small requests)."""
+    import numpy as np
+
+    import oracle
+    from paper_1407_2343_gb300 import serve
+
+    n = a.serve_requests
+    pool = serve.make_pool()
+    # capacity of the plain path: everything arrives at once
+    cap_sched = serve.make_schedule(n, rate=1e9, seed=5, pool=pool)
+    serve.run_plain(cap_sched[: max(4, n // 10)], dev)          # warm-up
+    cap = serve.run_plain(serve.make_schedule(n, rate=1e9, seed=5, pool=pool), dev).summary()["images_per_s"]
+    sweep = []
+    worst_vs_plain = 0.0
+    served_ref = None
+    for frac in (0.2, 0.5, 1.0, 1.5):
+        rate = frac * cap
+        sp = serve.make_schedule(n, rate=rate, seed=6, pool=pool)
+        ss = serve.make_schedule(n, rate=rate, seed=6, pool=pool)
+        p = serve.run_plain(sp, dev).summary()
+        s = serve.Server(dev).run(ss).summary()
+        for x, y in zip(sp, ss):
+            worst_vs_plain = max(worst_vs_plain, float(np.abs(x.out.numpy() - y.out.numpy()).max()))
+        sweep.append({"rate_frac_of_plain_capacity": frac, "rate_per_s": rate, "plain": p, "served": s})
+        served_ref = ss
+    # oracle on a sample of the small requests of the last schedule
+    worst_vs_oracle, checked = 0.0, 0
+    for r in served_ref:
+        if r.shape[0] > 512 or checked >= 4:
+            continue
+        ref, _ = oracle.snlm(r.img.numpy().astype(np.float64), r.S, r.K, r.h, r.profile, r.beta, r.order, r.sigma)
+        worst_vs_oracle = max(worst_vs_oracle, float(np.abs(r.out.numpy() - ref).max()))
+        checked += 1
+    return {"workload": f"{n} requests per point, Poisson arrivals, sizes 128..4096 squared with weights "
+                        ".3/.3/.2/.15/.05, S in {5,10,15,20}, K in {2,3,5}, box/gauss, RC/CR/AVG/SURE, u8/f16",
+            "plain_capacity_images_per_s": cap, "sweep": sweep,
+            "max_abs_served_vs_plain": worst_vs_plain, "max_abs_served_vs_oracle": worst_vs_oracle,
+            "oracle_checked_requests": checked}
+
+
 def run_ours(a):
     import torch
 
@@ -324,6 +433,12 @@ def run_ours(a):
         line["e2e"] = {"value": world * n_e2e * px / float(t.item()) / 1e6, "unit": "Mpixel/s",
                        "h2d_bytes_per_step": int(img_np.nbytes), "d2h_bytes_per_step": int(H * W * 4),
                        "steps": n_e2e, "api": "snlm_denoise_host (pinned host buffers)"}
+
+    if not a.no_batch:
+        line["batched"] = measure_batched(a, dev, stream)
+
+    if not a.no_serve and rank == 0:
+        line["served"] = measure_served(a, dev)
 
     if rank == 0 and not a.no_cpu_baseline:
         v, cores, desc, _, _ = cpu_oracle_rate(a, target_s=6.0)

@@ -539,11 +539,10 @@ int snlm_batch_plan_upload(snlm_batch_plan *P, void *workspace, size_t bytes, vo
         }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the host copy is staged by the runtime before cudaMemcpyAsync returns
+    // from pageable memory the runtime stages the source before cudaMemcpyAsync
+    // returns, so the local table may go out of scope right after
     cudaError_t e = cudaMemcpyAsync(base + P->jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return status_of(e);
     // kernel attributes and persistent grid sizes (every CTA resident)

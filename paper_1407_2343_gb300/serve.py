@@ -1,0 +1,245 @@
+"""Continuous-batching service for denoise requests, and its plain per-request
+counterpart.
+
+A request carries its own image (host memory), S, K, h, profile and order. The
+server replays an arrival schedule against the wall clock and loops:
+
+1. admission: arrived requests are admitted in arrival order while their device
+   footprint (input, output, their share of batch scratch) fits the memory budget
+   (a fraction of the free HBM when the server starts, or an explicit cap); the
+   input is copied host-to-device on an upload stream;
+2. step: all admitted requests not yet launched become one batch plan (the native
+   persistent launch over their tile units), launched on one of `streams`
+   rotating streams after their uploads; a step may start while earlier steps are
+   still running, so requests that arrive during a step overlap with it on the GPU;
+3. retirement: a finished step's outputs are copied back to pinned host buffers,
+   its memory is released and each request's latency (arrival to result in host
+   memory) is recorded.
+
+The plain path serves the same schedule one request at a time with
+snlm_denoise_host-style calls (copy in, denoise, copy out).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import api, synth
+
+SIZES = (128, 512, 1024, 2048, 4096)
+SIZE_WEIGHTS = (0.3, 0.3, 0.2, 0.15, 0.05)
+
+
+@dataclass
+class Request:
+    rid: int
+    img: object                 # pinned host tensor (H, W): uint8 / float16 / float32
+    S: int
+    K: int
+    h: float
+    profile: str
+    order: str
+    sigma: float
+    beta: float
+    t_arrival: float            # seconds from the start of the schedule
+    # filled by a run
+    out: object = None          # pinned host float32 result
+    t_done: float = math.nan
+    step: int = -1
+
+    @property
+    def shape(self):
+        return tuple(self.img.shape)
+
+    def latency(self):
+        return self.t_done - self.t_arrival
+
+
+def make_pool(sizes=SIZES, pool_per_size: int = 2, pin: bool = True):
+    """A small pool of synthetic noisy scenes per size (u8 and f16), shared by
+    the requests of a schedule (read-only)."""
+    import torch
+
+    pool = {}
+    for s in sizes:
+        for k in range(pool_per_size):
+            sigma = 10.0 + 40.0 * ((k + 1) / (pool_per_size + 1))
+            dt = "u8" if k % 2 == 0 else "f16"
+            img = torch.from_numpy(synth.noisy_image(s, s, sigma, seed=10 * s + k, dtype=dt))
+            pool[(s, k)] = (img.pin_memory() if pin else img, sigma)
+    return pool
+
+
+def make_schedule(n: int, rate: float, seed: int = 0, sizes=SIZES, weights=SIZE_WEIGHTS, pool_per_size: int = 2,
+                  pin: bool = True, pool=None):
+    """n requests with Poisson arrivals at `rate` per second. Images come from a
+    small pool of synthetic scenes per size (shared, read-only); each request
+    draws its own S, K, profile, order and sigma (h from the default rule)."""
+    rng = np.random.default_rng(seed)
+    if pool is None:
+        pool = make_pool(sizes, pool_per_size, pin)
+    t = 0.0
+    reqs = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        s = int(rng.choice(sizes, p=np.asarray(weights) / np.sum(weights)))
+        img, sigma = pool[(s, int(rng.integers(pool_per_size)))]
+        S = int(rng.choice([5, 10, 15, 20]))
+        K = int(rng.choice([2, 3, 5]))
+        profile = str(rng.choice(["box", "gauss"]))
+        order = str(rng.choice(["RC", "CR", "AVG", "SURE"]))
+        beta = K / 2.0
+        g = np.exp(-(np.arange(-K, K + 1) ** 2) / (2.0 * beta * beta)) if profile == "gauss" else np.ones(2 * K + 1)
+        h = float(sigma * math.sqrt(g.sum()))   # the default rule h = sigma sqrt(sum_k g(k))
+        reqs.append(Request(i, img, S, K, h, profile, order, sigma, beta, t))
+    return reqs
+
+
+def _footprint(r: Request) -> int:
+    H, W = r.shape
+    # input + output + the batch scratch of the request (intermediates of its order)
+    return r.img.element_size() * H * W + 4 * H * W + api.snlm_workspace_bytes(H, W, r.order)
+
+
+@dataclass
+class ServeStats:
+    latencies: list = field(default_factory=list)
+    steps: int = 0
+    max_inflight: int = 0
+    max_batch: int = 0
+    wall: float = 0.0
+    images: int = 0
+    max_used: int = 0           # peak device bytes of admitted requests
+
+    def summary(self):
+        lat = np.asarray(self.latencies) * 1e3
+        return {"images": self.images, "wall_s": self.wall, "images_per_s": self.images / self.wall if self.wall else 0,
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "mean_ms": float(lat.mean()) if len(lat) else None, "steps": self.steps,
+                "max_batch": self.max_batch, "max_inflight_steps": self.max_inflight,
+                "peak_admitted_bytes": self.max_used}
+
+
+class Server:
+    """The continuous-batching loop (single host thread)."""
+
+    def __init__(self, device=None, mem_budget: int | None = None, mem_fraction: float = 0.5, streams: int = 2,
+                 max_batch: int = 256, ctas_per_sm: int = 0):
+        import torch
+
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        self.budget = int(mem_budget if mem_budget is not None else free * mem_fraction)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(max(1, streams))]
+        self.upload = torch.cuda.Stream(self.dev)
+        self.max_batch = max_batch
+        self.ctas_per_sm = ctas_per_sm
+
+    def run(self, schedule, stats: ServeStats | None = None):
+        import torch
+
+        from .batch import Batch
+
+        stats = stats or ServeStats()
+        pending = list(schedule)          # in arrival order
+        pi = 0
+        admitted = []                     # (req, dev_in, dev_out, event)
+        inflight = []                     # (batch, event, [(req, dev_in, dev_out)], bytes)
+        used = 0
+        nstream = 0
+        t0 = time.perf_counter()
+        while pi < len(pending) or admitted or inflight:
+            now = time.perf_counter() - t0
+            # 1. admission
+            while pi < len(pending) and pending[pi].t_arrival <= now and len(admitted) < self.max_batch:
+                r = pending[pi]
+                need = _footprint(r)
+                if need > self.budget:
+                    raise ValueError(f"request {r.rid} needs {need} bytes, more than the whole budget")
+                if used + need > self.budget:
+                    break                 # wait for memory to free up
+                with torch.cuda.stream(self.upload):
+                    d_in = r.img.to(self.dev, non_blocking=True)
+                    d_out = torch.empty(r.shape, dtype=torch.float32, device=self.dev)
+                    ev = torch.cuda.Event()
+                    ev.record(self.upload)
+                used += need
+                stats.max_used = max(stats.max_used, used)
+                admitted.append((r, d_in, d_out, ev, need))
+                pi += 1
+            # 2. launch a step over everything admitted
+            if admitted and len(inflight) < len(self.streams):
+                st = self.streams[nstream % len(self.streams)]
+                nstream += 1
+                for (_, _, _, ev, _) in admitted:
+                    st.wait_event(ev)
+                reqs = [dict(img=d_in, out=d_out, S=r.S, K=r.K, h=r.h, profile=r.profile, order=r.order,
+                             sigma=r.sigma, beta=r.beta) for (r, d_in, d_out, _, _) in admitted]
+                with torch.cuda.stream(st):
+                    b = Batch(reqs, ctas_per_sm=self.ctas_per_sm, stream=st)
+                    b.run(st)
+                    done = torch.cuda.Event()
+                    done.record(st)
+                for (r, _, _, _, _) in admitted:
+                    r.step = stats.steps
+                inflight.append((b, done, admitted, st))
+                stats.steps += 1
+                stats.max_batch = max(stats.max_batch, len(admitted))
+                stats.max_inflight = max(stats.max_inflight, len(inflight))
+                admitted = []
+            # 3. retire finished steps (in launch order)
+            while inflight and inflight[0][1].query():
+                b, done, members, st = inflight.pop(0)
+                if b.status(st) != api.OK:
+                    raise RuntimeError("a batch step reported a timed-out dependency wait")
+                with torch.cuda.stream(st):
+                    for (r, d_in, d_out, _, need) in members:
+                        host = torch.empty(r.shape, dtype=torch.float32).pin_memory()
+                        host.copy_(d_out, non_blocking=True)
+                        r.out = host
+                st.synchronize()
+                t_done = time.perf_counter() - t0
+                for (r, d_in, d_out, _, need) in members:
+                    r.t_done = t_done
+                    stats.latencies.append(r.latency())
+                    used -= need
+                stats.images += len(members)
+                b.close()
+            if pi < len(pending) and not admitted and not inflight:
+                # idle until the next arrival
+                wait = pending[pi].t_arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+        stats.wall = time.perf_counter() - t0
+        return stats
+
+
+def run_plain(schedule, device=None, stats: ServeStats | None = None):
+    """Serve the schedule one request at a time (FIFO): copy in, snlm_denoise,
+    copy out, wait."""
+    import torch
+
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    stats = stats or ServeStats()
+    st = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    for r in schedule:
+        now = time.perf_counter() - t0
+        if r.t_arrival > now:
+            time.sleep(r.t_arrival - now)
+        with torch.cuda.stream(st):
+            d_in = r.img.to(dev, non_blocking=True)
+            out = api.snlm_denoise(d_in, r.S, r.K, r.h, r.profile, r.order, r.sigma, r.beta, stream=st)
+            host = torch.empty(r.shape, dtype=torch.float32).pin_memory()
+            host.copy_(out, non_blocking=True)
+        st.synchronize()
+        r.out = host
+        r.t_done = time.perf_counter() - t0
+        stats.latencies.append(r.latency())
+        stats.images += 1
+    stats.wall = time.perf_counter() - t0
+    return stats

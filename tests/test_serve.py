@@ -1,0 +1,83 @@
+"""The continuous-batching service: schedule generation (CPU), and on the GPU the
+result of every request alone equals its result in the mix, admission under a
+memory cap, and rejection of a request larger than the whole budget."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1407_2343_gb300 import serve
+
+TOL = 1e-4
+
+
+def test_schedule_statistics():
+    reqs = serve.make_schedule(400, rate=1000.0, seed=3, sizes=(16, 32, 48), weights=(0.5, 0.3, 0.2), pin=False)
+    t = np.array([r.t_arrival for r in reqs])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1e-3) < 0.2e-3          # Poisson at 1000/s
+    frac = np.mean([r.shape[0] == 16 for r in reqs])
+    assert abs(frac - 0.5) < 0.08
+    for r in reqs:
+        assert r.S in (5, 10, 15, 20) and r.K in (2, 3, 5)
+        assert r.profile in ("box", "gauss") and r.order in ("RC", "CR", "AVG", "SURE")
+        if r.profile == "box":
+            assert r.h == pytest.approx(r.sigma * math.sqrt(2 * r.K + 1), rel=1e-6)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_2343_gb300 import _lib, build
+
+    build.build()
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def alone(r, dev):
+    from paper_1407_2343_gb300 import api
+
+    out = api.snlm_denoise(r.img.to(dev), r.S, r.K, r.h, r.profile, r.order, r.sigma, r.beta)
+    return out.cpu().numpy()
+
+
+@pytest.mark.gpu
+def test_results_alone_equal_results_in_the_mix(dev):
+    reqs = serve.make_schedule(40, rate=4000.0, seed=1, sizes=(128, 256, 512), weights=(0.5, 0.3, 0.2))
+    stats = serve.Server(dev).run(reqs)
+    assert stats.images == len(reqs)
+    assert stats.max_batch > 1                         # requests were batched together
+    for r in reqs:
+        ref = alone(r, dev)
+        got = r.out.numpy()
+        if r.order == "SURE":
+            assert np.abs(got - ref).max() <= TOL
+        else:
+            assert np.array_equal(got, ref), (r.rid, r.order)
+    s = stats.summary()
+    assert s["p50_ms"] > 0 and s["p99_ms"] >= s["p50_ms"]
+
+
+@pytest.mark.gpu
+def test_admission_under_a_memory_cap(dev):
+    from paper_1407_2343_gb300 import api
+
+    reqs = serve.make_schedule(12, rate=10000.0, seed=2, sizes=(256,), weights=(1.0,))
+    cap = max(serve._footprint(r) for r in reqs) * 2 + 1
+    stats = serve.Server(dev, mem_budget=cap).run(reqs)
+    assert stats.images == 12
+    assert stats.max_used <= cap                       # never more than the cap admitted
+    assert stats.steps >= 4                            # so the requests went through in several steps
+    for r in reqs[:4]:
+        ref = alone(r, dev)
+        tol = TOL if r.order == "SURE" else 0.0
+        assert np.abs(r.out.numpy() - ref).max() <= tol
+    big = serve.make_schedule(1, rate=1.0, seed=4, sizes=(512,), weights=(1.0,))
+    with pytest.raises(ValueError):
+        serve.Server(dev, mem_budget=1024).run(big)
+    assert api.snlm_version() >= 100
