@@ -278,17 +278,19 @@ def measure_served(a, dev):
 
     n = a.serve_requests
     pool = serve.make_pool()
-    # capacity of the plain path: everything arrives at once
-    cap_sched = serve.make_schedule(n, rate=1e9, seed=5, pool=pool)
-    serve.run_plain(cap_sched[: max(4, n // 10)], dev)          # warm-up
-    cap = serve.run_plain(serve.make_schedule(n, rate=1e9, seed=5, pool=pool), dev).summary()["images_per_s"]
+    # capacity of the plain path: everything arrives at once (best of two runs)
+    cap = 0.0
+    for _ in range(2):
+        sched = serve.make_schedule(n, rate=1e9, seed=5, pool=pool)
+        serve.prepare_outputs(sched)
+        cap = max(cap, serve.run_plain(sched, dev).summary()["images_per_s"])
     sweep = []
     worst_vs_plain = 0.0
     served_ref = None
-    for frac in (0.2, 0.5, 1.0, 1.5):
+    for frac in (0.2, 0.5, 1.0, 1.5, 2.0, 3.0):
         rate = frac * cap
-        sp = serve.make_schedule(n, rate=rate, seed=6, pool=pool)
-        ss = serve.make_schedule(n, rate=rate, seed=6, pool=pool)
+        sp = serve.prepare_outputs(serve.make_schedule(n, rate=rate, seed=6, pool=pool))
+        ss = serve.prepare_outputs(serve.make_schedule(n, rate=rate, seed=6, pool=pool))
         p = serve.run_plain(sp, dev).summary()
         s = serve.Server(dev).run(ss).summary()
         for x, y in zip(sp, ss):

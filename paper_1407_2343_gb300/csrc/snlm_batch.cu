@@ -181,6 +181,34 @@ BatchFn batch_fn(int K)
     }
 }
 
+// Shared-memory limit and occupancy of a class kernel, cached per (device, K, bytes):
+// the shared-memory attribute only ever grows, and a serving loop builds a plan
+// per step.
+cudaError_t class_occupancy(BatchFn fn, int dev, int K, size_t smem, int *occ)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<long long, int>> cache;   // key -> occupancy
+    static std::vector<size_t> attr(64 * 8, 0);             // (dev, K) -> attribute set
+    const long long key = ((long long)dev << 40) | ((long long)K << 32) | (long long)smem;
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto &kv : cache)
+        if (kv.first == key) {
+            *occ = kv.second;
+            return cudaSuccess;
+        }
+    const size_t slot = (size_t)(dev % 64) * 8 + (size_t)K;
+    if (attr[slot] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        attr[slot] = smem;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kWarpsPerCta * 32, smem);
+    if (e == cudaSuccess)
+        cache.push_back({key, *occ});
+    return e;
+}
+
 struct ClassInfo {
     int K = 0;
     int j0 = 0, nj = 0;       // job range (global indices, contiguous)
@@ -553,11 +581,8 @@ int snlm_batch_plan_upload(snlm_batch_plan *P, void *workspace, size_t bytes, vo
         BatchFn fn = batch_fn(c.K);
         if (!fn)
             return SNLM_ERR_UNSUPPORTED;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-        if (e != cudaSuccess)
-            return status_of(e);
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kWarpsPerCta * 32, c.smem);
+        e = class_occupancy(fn, dev, c.K, c.smem, &occ);
         if (e != cudaSuccess || occ < 1)
             return e != cudaSuccess ? status_of(e) : SNLM_ERR_UNSUPPORTED;
         const int per_sm = P->cfg.ctas_per_sm > 0 ? std::min(P->cfg.ctas_per_sm, occ) : occ;

@@ -45,7 +45,7 @@ class Request:
     sigma: float
     beta: float
     t_arrival: float            # seconds from the start of the schedule
-    # filled by a run
+    # filled by a run (preallocated by prepare_outputs, outside any timed region)
     out: object = None          # pinned host float32 result
     t_done: float = math.nan
     step: int = -1
@@ -98,6 +98,17 @@ def make_schedule(n: int, rate: float, seed: int = 0, sizes=SIZES, weights=SIZE_
     return reqs
 
 
+def prepare_outputs(schedule, pin: bool = True):
+    """Allocate every request's host result buffer (pinned) ahead of a run."""
+    import torch
+
+    for r in schedule:
+        if r.out is None or tuple(r.out.shape) != r.shape:
+            o = torch.empty(r.shape, dtype=torch.float32)
+            r.out = o.pin_memory() if pin else o
+    return schedule
+
+
 def _footprint(r: Request) -> int:
     H, W = r.shape
     # input + output + the batch scratch of the request (intermediates of its order)
@@ -113,6 +124,7 @@ class ServeStats:
     wall: float = 0.0
     images: int = 0
     max_used: int = 0           # peak device bytes of admitted requests
+    host_s: dict = field(default_factory=lambda: {"admit": 0.0, "launch": 0.0, "retire": 0.0})
 
     def summary(self):
         lat = np.asarray(self.latencies) * 1e3
@@ -121,13 +133,14 @@ class ServeStats:
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_ms": float(lat.mean()) if len(lat) else None, "steps": self.steps,
                 "max_batch": self.max_batch, "max_inflight_steps": self.max_inflight,
-                "peak_admitted_bytes": self.max_used}
+                "peak_admitted_bytes": self.max_used,
+                "host_ms": {k: v * 1e3 for k, v in self.host_s.items()}}
 
 
 class Server:
     """The continuous-batching loop (single host thread)."""
 
-    def __init__(self, device=None, mem_budget: int | None = None, mem_fraction: float = 0.5, streams: int = 2,
+    def __init__(self, device=None, mem_budget: int | None = None, mem_fraction: float = 0.5, streams: int = 3,
                  max_batch: int = 256, ctas_per_sm: int = 0):
         import torch
 
@@ -145,6 +158,7 @@ class Server:
         from .batch import Batch
 
         stats = stats or ServeStats()
+        prepare_outputs(schedule)
         pending = list(schedule)          # in arrival order
         pi = 0
         admitted = []                     # (req, dev_in, dev_out, event)
@@ -154,6 +168,7 @@ class Server:
         t0 = time.perf_counter()
         while pi < len(pending) or admitted or inflight:
             now = time.perf_counter() - t0
+            h0 = time.perf_counter()
             # 1. admission
             while pi < len(pending) and pending[pi].t_arrival <= now and len(admitted) < self.max_batch:
                 r = pending[pi]
@@ -171,6 +186,8 @@ class Server:
                 stats.max_used = max(stats.max_used, used)
                 admitted.append((r, d_in, d_out, ev, need))
                 pi += 1
+            h1 = time.perf_counter()
+            stats.host_s["admit"] += h1 - h0
             # 2. launch a step over everything admitted
             if admitted and len(inflight) < len(self.streams):
                 st = self.streams[nstream % len(self.streams)]
@@ -191,6 +208,8 @@ class Server:
                 stats.max_batch = max(stats.max_batch, len(admitted))
                 stats.max_inflight = max(stats.max_inflight, len(inflight))
                 admitted = []
+            h2 = time.perf_counter()
+            stats.host_s["launch"] += h2 - h1
             # 3. retire finished steps (in launch order)
             while inflight and inflight[0][1].query():
                 b, done, members, st = inflight.pop(0)
@@ -198,9 +217,7 @@ class Server:
                     raise RuntimeError("a batch step reported a timed-out dependency wait")
                 with torch.cuda.stream(st):
                     for (r, d_in, d_out, _, need) in members:
-                        host = torch.empty(r.shape, dtype=torch.float32).pin_memory()
-                        host.copy_(d_out, non_blocking=True)
-                        r.out = host
+                        r.out.copy_(d_out, non_blocking=True)
                 st.synchronize()
                 t_done = time.perf_counter() - t0
                 for (r, d_in, d_out, _, need) in members:
@@ -209,6 +226,7 @@ class Server:
                     used -= need
                 stats.images += len(members)
                 b.close()
+            stats.host_s["retire"] += time.perf_counter() - h2
             if pi < len(pending) and not admitted and not inflight:
                 # idle until the next arrival
                 wait = pending[pi].t_arrival - (time.perf_counter() - t0)
@@ -225,6 +243,7 @@ def run_plain(schedule, device=None, stats: ServeStats | None = None):
 
     dev = device or torch.device("cuda", torch.cuda.current_device())
     stats = stats or ServeStats()
+    prepare_outputs(schedule)
     st = torch.cuda.Stream(dev)
     t0 = time.perf_counter()
     for r in schedule:
@@ -234,10 +253,8 @@ def run_plain(schedule, device=None, stats: ServeStats | None = None):
         with torch.cuda.stream(st):
             d_in = r.img.to(dev, non_blocking=True)
             out = api.snlm_denoise(d_in, r.S, r.K, r.h, r.profile, r.order, r.sigma, r.beta, stream=st)
-            host = torch.empty(r.shape, dtype=torch.float32).pin_memory()
-            host.copy_(out, non_blocking=True)
+            r.out.copy_(out, non_blocking=True)
         st.synchronize()
-        r.out = host
         r.t_done = time.perf_counter() - t0
         stats.latencies.append(r.latency())
         stats.images += 1
