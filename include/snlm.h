@@ -233,7 +233,8 @@ void snlm_batch_plan_destroy(snlm_batch_plan *plan);
  * kinds[i] (an snlm_kernel_kind) and ms[i] (device time between the events).
  * The low byte of a kind is an snlm_kernel_kind; bits 8 and up tell how the
  * patch distances were reduced in that launch (0 running sum, 1 block sums,
- * 2 weighted taps); snlm_kernel_name spells both out (e.g. "row_pass/slide").
+ * 2 weighted taps), and bit 12 is set when the pass ran the TMA kernel;
+ * snlm_kernel_name spells them out (e.g. "row_pass/slide", "col_pass_sure/block/tma").
  * Tracing is process-wide; do not enable it while a stream is being captured
  * into a CUDA graph. snlm_trace_read waits for the recorded events, copies at
  * most max_records records (oldest first), sets *n_records to the number copied
@@ -255,6 +256,45 @@ typedef enum {
 int snlm_trace_enable(int enable);
 int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records);
 const char *snlm_kernel_name(int kind);
+
+/*
+ * Process-wide options (no counterpart in the paper).
+ *
+ * SNLM_OPT_TMA (default 0): 1 makes the per-image passes (snlm_denoise*, SURE
+ *   order included) run the persistent kernel that moves line windows and tile
+ *   inputs with TMA bulk tensor copies whenever every array a pass reads allows
+ *   it: a 16-byte-aligned base address, unit stride along the lines or across
+ *   them, and the other stride a multiple of 16 bytes (e.g. an 8-bit image whose
+ *   pitch is a multiple of 16, float intermediates of width a multiple of 4).
+ *   Other passes, snlm_nlm_1d and the batch kernels always gather their samples
+ *   with loads. Both kernels give the same results (the tests hold both to the
+ *   oracle's tolerance); the gathering kernel is the faster one on GB300 today.
+ * SNLM_OPT_WAIT_LIMIT_US (default 2,000,000): bound of every device-side wait of
+ *   the TMA passes, in microseconds (1 .. 60,000,000).
+ * SNLM_OPT_INJECT_WAIT_TIMEOUT (default 0): fault injection for tests: the next
+ *   `value` TMA pass launches wait for bytes that never arrive, so their waits run
+ *   out (no device fault); their outputs are NaN and snlm_device_error reports it.
+ *
+ * snlm_set_option returns SNLM_OK or SNLM_ERR_ARG; snlm_get_option returns the
+ * value, or -1 for an unknown option.
+ */
+typedef enum {
+    SNLM_OPT_TMA = 0,
+    SNLM_OPT_WAIT_LIMIT_US = 1,
+    SNLM_OPT_INJECT_WAIT_TIMEOUT = 2
+} snlm_option;
+
+int snlm_set_option(int option, long long value);
+long long snlm_get_option(int option);
+
+/*
+ * Device-side failure record of the current device. Waits for the work queued on
+ * `stream` (NULL: the legacy default stream), then returns SNLM_ERR_TIMEOUT if a
+ * bounded wait of a TMA pass gave up since the last call (every output of the
+ * units it could not finish was set to NaN), SNLM_ERR_CUDA if the stream failed,
+ * else SNLM_OK; the record is cleared. snlm_denoise_host checks it itself.
+ */
+int snlm_device_error(void *stream);
 
 #ifdef __cplusplus
 }

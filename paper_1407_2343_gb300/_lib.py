@@ -95,6 +95,12 @@ def load(build_if_missing: bool = False):
         lib.snlm_trace_read.restype = ci
         lib.snlm_kernel_name.argtypes = [ci]
         lib.snlm_kernel_name.restype = ctypes.c_char_p
+        lib.snlm_set_option.argtypes = [ci, ctypes.c_longlong]
+        lib.snlm_set_option.restype = ci
+        lib.snlm_get_option.argtypes = [ci]
+        lib.snlm_get_option.restype = ctypes.c_longlong
+        lib.snlm_device_error.argtypes = [vp]
+        lib.snlm_device_error.restype = ci
         del fp, dp
         _lib = lib
         return lib
@@ -107,4 +113,5 @@ EXPORTED = [
     "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc", "snlm_batch_plan_create",
     "snlm_batch_plan_workspace_bytes", "snlm_batch_plan_upload", "snlm_batch_plan_launch",
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
+    "snlm_set_option", "snlm_get_option", "snlm_device_error",
 ]

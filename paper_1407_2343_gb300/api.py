@@ -218,6 +218,23 @@ def snlm_kernel_name(kind: int) -> str:
     return _lib.load().snlm_kernel_name(int(kind)).decode()
 
 
+OPT_TMA, OPT_WAIT_LIMIT_US, OPT_INJECT_WAIT_TIMEOUT = 0, 1, 2
+
+
+def snlm_set_option(option: int, value: int):
+    _check(_lib.load().snlm_set_option(int(option), int(value)), "snlm_set_option")
+
+
+def snlm_get_option(option: int) -> int:
+    return int(_lib.load().snlm_get_option(int(option)))
+
+
+def snlm_device_error(stream=None) -> int:
+    """Wait for `stream`, return (and clear) the device-side failure record:
+    OK, or ERR_TIMEOUT when a bounded wait of a TMA pass gave up."""
+    return int(_lib.load().snlm_device_error(_stream_ptr(stream)))
+
+
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 

@@ -173,9 +173,15 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     a.partials = ps.partials;
     a.aux_f = ps.aux_f;
     a.aux_rc = ps.aux_rc;
+    finish_pass_args(a);
     const int dm = dist_mode_for(ps.src.dtype, profile);
-    TraceScope ts(((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) + (sure ? 2 : 0)) | (dm << 8), st);
-    return dispatch_pass(K, a, dm, sure, st);
+    TmaPass t;
+    int grid = 0;
+    const bool tma = plan_pass_tma(K, a, dm, sure, &t, &grid);
+    TraceScope ts(((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) + (sure ? 2 : 0)) | (dm << 8) |
+                      (tma ? kTraceTma : 0),
+                  st);
+    return tma ? launch_planned_tma(K, a, t, dm, sure, grid, st) : dispatch_pass(K, a, dm, sure, st);
 }
 
 int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
@@ -365,7 +371,10 @@ int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, 
     e = cudaMemcpyAsync(out_host, dout, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess)
         return status_of(e);
-    return status_of(cudaStreamSynchronize(st));
+    rc = status_of(cudaStreamSynchronize(st));
+    if (rc != SNLM_OK)
+        return rc;
+    return snlm_device_error(st);
 }
 
 int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_step,
@@ -411,6 +420,7 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
     a.delta_out = delta_out;
     a.aux_f = Lines{nullptr, DT_F32, 0, 0};
     a.aux_rc = Lines{nullptr, DT_F32, 0, 0};
+    finish_pass_args(a);
     const int dm = dist_mode_for(dtype, profile);
     TraceScope ts(SNLM_K_LINE_PASS | (dm << 8), static_cast<cudaStream_t>(stream));
     return status_of(dispatch_pass(K, a, dm, sure, static_cast<cudaStream_t>(stream)));
@@ -483,8 +493,9 @@ int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records)
 
 const char *snlm_kernel_name(int kind)
 {
-    // low byte: snlm_kernel_kind; bits 8..: how the patch distances were reduced
-    static const char *names[9][4] = {
+    // low byte: snlm_kernel_kind; bits 8..11: how the patch distances were
+    // reduced; bit 12: the pass moved its data with TMA bulk tensor copies
+    static const char *names[10][4] = {
         {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
         {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
         {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
@@ -494,11 +505,20 @@ const char *snlm_kernel_name(int kind)
         {"set_theta", "set_theta", "set_theta", "set_theta"},
         {"patch_dist", "patch_dist/slide", "patch_dist/block", "patch_dist/fir"},
         {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir"},
+        {"batch", "batch", "batch", "batch"},
     };
-    const int base = kind & 0xff, dm = kind >> 8;
-    if (base < 0 || base > 8 || dm < 0 || dm > 2)
+    static const char *tma_names[4][3] = {
+        {"row_pass/slide/tma", "row_pass/block/tma", "row_pass/fir/tma"},
+        {"col_pass/slide/tma", "col_pass/block/tma", "col_pass/fir/tma"},
+        {"row_pass_sure/slide/tma", "row_pass_sure/block/tma", "row_pass_sure/fir/tma"},
+        {"col_pass_sure/slide/tma", "col_pass_sure/block/tma", "col_pass_sure/fir/tma"},
+    };
+    const int base = kind & 0xff, dm = (kind >> 8) & 0xf, tma = (kind >> 12) & 1;
+    if (kind < 0 || base > 9 || dm > 2 || (kind >> 13) != 0)
         return "unknown";
-    const bool has_dm = base <= 3 || base >= 7;
+    if (tma)
+        return base <= 3 ? tma_names[base][dm] : "unknown";
+    const bool has_dm = base <= 3 || base == 7 || base == 8;
     return names[base][has_dm ? dm + 1 : 0];
 }
 

@@ -280,6 +280,7 @@ PassArgs pass_args(int axis, int H, int W, const Lines &src, float *dst, int S, 
     a.out_elem_step = axis == 0 ? 1 : W;
     a.aux_f = Lines{nullptr, DT_F32, 0, 0};
     a.aux_rc = Lines{nullptr, DT_F32, 0, 0};
+    finish_pass_args(a);
     return a;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libsnlm translation units (host + device).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +32,7 @@ struct Lines {
 struct PassArgs {
     Lines src;                  // input samples of the pass
     int n_lines, N, S;
+    int tiles;                  // tiles per line: div_up(N, tile_positions(S)) (set by finish_pass_args)
     float c2;                   // -log2(e) / h^2, so w = 2^(c2 * d^2)
     float h2;                   // h^2 (divergence only)
     float g[2 * kMaxK + 1];     // patch profile g(k), k = -K..K
@@ -41,7 +43,7 @@ struct PassArgs {
     float *delta_out;           // optional (SURE kernels): chained derivative out
     double *partials;           // optional: kPartials sums per CTA (see below)
     Lines aux_f;                // the noisy input image f, viewed like dst
-    Lines aux_rc;               // f_rc, viewed like dst: when given, the SURE sums below are formed
+    Lines aux_rc;               // f_rc (float32), viewed like dst: when given, the SURE sums below are formed
     // Per-CTA partial sums (SURE). With m = (f_rc + fhat)/2 and d = (f_rc - fhat)/2
     // (fhat = f_cr in the last pass of the CR order):
     //   [0] sum m^2  [1] sum m d  [2] sum d^2  [3] sum f m  [4] sum f d  [5] sum delta_out
@@ -62,7 +64,7 @@ struct DistArgs {
 struct WarpLayout {
     int LF;        // line samples (padded)
     int LW;        // one stored-weight row (SURE, padded)
-    int LT;        // one tile-sized row (SURE delta in / out, padded)
+    int LT;        // one tile-sized row (blend, SURE delta in / out, f_rc, f; padded)
     int per_warp;  // total, multiple of 4
 };
 
@@ -80,8 +82,11 @@ __host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool 
     L.LW = (pad_index(32 * kRun) + 4) & ~3;
     L.LT = L.LW;
     int n = L.LF;
-    if (sure && !dist_only)
-        n += K * L.LW + 2 * L.LT;   // stored weights for |s| <= K, delta in, delta out
+    if (!dist_only) {
+        n += L.LT;                  // the blend input of the tile
+        if (sure)                   // stored weights for |s| <= K; delta in, delta out; f_rc and f
+            n += K * L.LW + 4 * L.LT;
+    }
     L.per_warp = (n + 3) & ~3;
     return L;
 }
@@ -93,7 +98,57 @@ __host__ __device__ inline int tile_positions(int S)
     return (32 - div_up(S, kRun)) * kRun;
 }
 
+// Fills the derived fields of a pass's arguments (after n_lines, N and S).
+inline void finish_pass_args(PassArgs &a) { a.tiles = div_up(a.N, tile_positions(a.S)); }
+
 template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
+// ---- Tensor-memory-accelerator (TMA) movement of a pass (sm_90+ bulk tensor copies).
+// Each array a pass reads (the line windows and the tile inputs of the epilogue)
+// gets a 2-D tensor map over (dim0, dim1) = (positions, lines) for row-like views
+// (TMA_ROWS) or (lines, positions) for column-like views (TMA_COLS), and a unit
+// loads boxes whose dim0 start is a multiple of 16 bytes. The landed element
+// (line w, position q) of a unit sits at element w*sw + q*sq + o of the view's
+// shared-memory area, o being the unit's alignment offset.
+enum TmaMode { TMA_NONE = 0, TMA_ROWS = 1, TMA_COLS = 2 };
+enum TmaArray { TMA_SRC = 0, TMA_DIN = 1, TMA_BLEND = 2, TMA_RC = 3, TMA_F = 4, TMA_ARRAYS = 5 };
+
+struct TmaView {
+    int mode;       // TmaMode
+    int dtype;      // DType of the elements
+    int esize;      // bytes per element
+    int align;      // elements per 16 bytes (dim0 coordinates are multiples of it)
+    int nb;         // boxes per line (ROWS) or along the positions (COLS)
+    int bw, bh;     // box extents along dim0 and dim1 (elements)
+    int sw, sq;     // element strides of the landed data between lines and positions
+    int bytes;      // bytes a unit's boxes deliver
+    int smem;       // shared-memory bytes reserved for them (multiple of 128)
+    int off;        // byte offset of that area in the CTA's dynamic shared memory
+};
+
+struct TmaPass {
+    CUtensorMap map[TMA_ARRAYS];    // src, delta_in, blend, aux_rc, aux_f
+    TmaView v[TMA_ARRAYS];          // v[TMA_SRC].off is window stage 0
+    int win_off1;                   // byte offset of window stage 1
+    int win_len;                    // window samples per line and unit
+    int units;                      // units of the pass (tile fastest)
+    int per_warp, LF, LW, LT;       // per-warp float layout: window, K weight rows, delta_out
+    int smem;                       // dynamic shared-memory bytes per CTA
+    unsigned long long wait_ns;     // bound of every barrier wait
+    unsigned *err;                  // receives SNLM_ERR_TIMEOUT when a wait gives up (may be NULL)
+    int inject;                     // test hook: units expect bytes that never arrive
+};
+
+template <int K> cudaError_t launch_pass_tma(const PassArgs &a, const TmaPass &t, int dist_mode, bool sure, int grid,
+                                             cudaStream_t st);
+template <int K> cudaError_t pass_tma_occupancy(int dist_mode, bool sure, int smem, int *ctas_per_sm);
+
+// Host side (snlm_tma_host.cu).
+bool plan_pass_tma(int K, const PassArgs &a, int dist_mode, bool sure, TmaPass *t, int *grid);
+cudaError_t launch_planned_tma(int K, const PassArgs &a, const TmaPass &t, int dist_mode, bool sure, int grid,
+                               cudaStream_t st);
+unsigned *device_error_word();
+constexpr int kTraceTma = 1 << 12;   // trace-kind flag: the launch used the TMA kernel
+
 template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);
 
 // scratch: 2 * kSolveScratchRecords * kPartials doubles

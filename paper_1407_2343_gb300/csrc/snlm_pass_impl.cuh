@@ -32,15 +32,24 @@
 
 namespace snlm {
 
-__device__ __forceinline__ int reflect_index(int x, int n)
+// Symmetric extension of a line of n samples (... f1 f0 | f0 f1 ... f_n-1 | f_n-1 ...),
+// for any x: the general case, kept out of line (it only runs for tiny lines).
+static __device__ __noinline__ int reflect_index_any(int x, int n)
 {
-    if (x >= 0 && x < n)
-        return x;
     const int p = 2 * n;
     int y = x % p;
     if (y < 0)
         y += p;
     return y < n ? y : p - 1 - y;
+}
+
+__device__ __forceinline__ int reflect_index(int x, int n)
+{
+    if (x >= 0 && x < n)
+        return x;
+    if (x >= -n && x < 2 * n)   // one reflection
+        return x < 0 ? -x - 1 : 2 * n - 1 - x;
+    return reflect_index_any(x, n);
 }
 
 __device__ __forceinline__ float load_at(const void *ptr, int dtype, unsigned off)
@@ -73,7 +82,33 @@ __device__ __forceinline__ void patch_distances(const float (&dl)[M + 2 * K], fl
                                                 const float *__restrict__ g)
 {
     constexpr int W = 2 * K + 1;
-    if constexpr (DM == DIST_SLIDE) {
+    if constexpr (DM != DIST_FIR && W >= M - 1) {
+        // Box profile, windows at least M - 1 wide: every window [m, m + 2K] contains
+        // the split point U = M - 1 or ends right before it, so it is the suffix
+        // [m, U - 1] plus the prefix [U, m + 2K]. Both parts are sums of squares that
+        // all belong to the window (no cancellation; exact for integer samples) and the
+        // cost equals a running sum's, with two short chains instead of one long one.
+        constexpr int U = M - 1;
+        float suf[U];
+        suf[U - 1] = dl[U - 1] * dl[U - 1];
+#pragma unroll
+        for (int u = U - 2; u >= 0; --u)
+            suf[u] = fmaf(dl[u], dl[u], suf[u + 1]);
+        float pre[M + 2 * K];
+        pre[U] = dl[U] * dl[U];
+#pragma unroll
+        for (int u = U + 1; u < M + 2 * K; ++u)
+            pre[u] = fmaf(dl[u], dl[u], pre[u - 1]);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (m >= U)
+                D[m] = pre[m + 2 * K];
+            else if (m + 2 * K < U)
+                D[m] = suf[m];
+            else
+                D[m] = suf[m] + pre[m + 2 * K];
+        }
+    } else if constexpr (DM == DIST_SLIDE) {
         // Running sum (box profile): two updates per step, whatever K is.
         float acc = 0.f;
 #pragma unroll
@@ -130,65 +165,395 @@ __device__ __forceinline__ void patch_distances(const float (&dl)[M + 2 * K], fl
     }
 }
 
-// Cooperative load of the CTA's line windows into shared memory:
-// buf(w)[pad_index(q)] = sample at position pos0 + q of line line0 + w
-// (reflected), q < len. Row-like views (elem_step == 1) are read along the line;
-// column-like views across lines, so consecutive threads touch consecutive
-// addresses.
-__device__ __forceinline__ void load_windows(float *smem, int per_warp, const Lines &v, int n_lines,
-                                             int N, int line0, int pos0, int len)
+// Gathers of the load phase. Thread (w, q0) of the CTA handles line line0 + w and
+// positions q = q0 + 32 b; row-like views (elem_step == 1) give each warp one line
+// (consecutive lanes on consecutive samples), column-like views give consecutive
+// threads consecutive lines of the same position. Every read of a gather is issued
+// before its values are used, so a CTA waits for about one memory round trip.
+__device__ __forceinline__ void gather_slot(bool row_like, int &w, int &q0)
 {
-    if (v.elem_step == 1) {
-        // one warp per line, consecutive lanes on consecutive samples
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int ln = line0 + w;
-        float *buf = smem + w * per_warp;
-        if (ln >= n_lines)
-            return;
-        const unsigned base = (unsigned)(ln * (int)v.line_step);
-        for (int q = lane; q < len; q += 32) {
+    w = row_like ? (int)(threadIdx.x >> 5) : (int)(threadIdx.x % kWarpsPerCta);
+    q0 = row_like ? (int)(threadIdx.x & 31) : (int)(threadIdx.x / kWarpsPerCta);
+}
+
+template <typename T>
+__device__ __forceinline__ float to_float(T v) { return (float)v; }
+template <>
+__device__ __forceinline__ float to_float<__half>(__half v) { return __half2float(v); }
+
+// Window samples: v[b] = sample at position pos0 + q (reflected), q < len.
+template <typename T, int NB>
+__device__ __forceinline__ void gather_window_t(float (&v)[NB], const T *ptr, unsigned base, int es, int N,
+                                                int pos0, int q0, int len)
+{
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int q = q0 + 32 * b;
+        if (q < len) {
             const int x = pos0 + q;
-            const int i = (x >= 0 && x < N) ? x : reflect_index(x, N);
-            buf[q + (q >> 3)] = load_at(v.ptr, v.dtype, base + (unsigned)i);
-        }
-    } else {
-        // columns: consecutive threads on consecutive lines of the same position
-        const int w = threadIdx.x % kWarpsPerCta;
-        const int ln = line0 + w;
-        if (ln >= n_lines)
-            return;
-        float *buf = smem + w * per_warp;
-        const int es = (int)v.elem_step;
-        const unsigned base = (unsigned)(ln * (int)v.line_step);
-        for (int q = threadIdx.x / kWarpsPerCta; q < len; q += blockDim.x / kWarpsPerCta) {
-            const int x = pos0 + q;
-            const int i = (x >= 0 && x < N) ? x : reflect_index(x, N);
-            buf[q + (q >> 3)] = load_at(v.ptr, v.dtype, base + (unsigned)(i * es));
+            const int i = reflect_index(x, N);
+            v[b] = to_float(__ldg(ptr + base + (unsigned)(i * es)));
         }
     }
 }
 
-// Cooperative load of a float image restricted to the tile (positions xa + q,
-// q < T), padded like the windows; `fill` where the position is past the line.
-__device__ __forceinline__ void load_tile(float *smem, int per_warp, int off, const float *img,
-                                          long long line_step, long long elem_step, int n_lines, int N,
-                                          int line0, int xa, int T, float fill)
+template <int NB>
+__device__ __forceinline__ void gather_window(float (&v)[NB], const Lines &src, int ln, int N, int pos0, int q0,
+                                              int len)
 {
-    if (elem_step == 1) {
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int ln = line0 + w;
-        float *buf = smem + w * per_warp + off;
-        const float *row = img + (ln < n_lines ? ln * (int)line_step : 0);
-        for (int q = lane; q < T; q += 32)
-            buf[q + (q >> 3)] = (ln < n_lines && xa + q < N) ? __ldg(row + xa + q) : fill;
+    const unsigned base = (unsigned)(ln * (int)src.line_step);
+    const int es = (int)src.elem_step;
+    if (src.dtype == DT_U8)
+        gather_window_t<unsigned char, NB>(v, static_cast<const unsigned char *>(src.ptr), base, es, N, pos0, q0,
+                                           len);
+    else if (src.dtype == DT_F16)
+        gather_window_t<__half, NB>(v, static_cast<const __half *>(src.ptr), base, es, N, pos0, q0, len);
+    else
+        gather_window_t<float, NB>(v, static_cast<const float *>(src.ptr), base, es, N, pos0, q0, len);
+}
+
+// Tile samples of a float image: v[b] = img at position xa + q of the line, q < T;
+// `fill` past the end of the line.
+template <int NB>
+__device__ __forceinline__ void gather_tile(float (&v)[NB], const float *img, long long line_step,
+                                            long long elem_step, int ln, int N, int xa, int q0, int T, float fill)
+{
+    const float *row = img + ln * (int)line_step;
+    const int es = (int)elem_step;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int q = q0 + 32 * b;
+        v[b] = fill;
+        if (q < T && xa + q < N)
+            v[b] = __ldg(row + (xa + q) * es);
+    }
+}
+
+// Same for a strided view of any sample type (zero past the end of the line).
+template <typename T, int NB>
+__device__ __forceinline__ void gather_tile_t(float (&v)[NB], const T *ptr, unsigned base, int es, int N, int xa,
+                                              int q0, int T_)
+{
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int q = q0 + 32 * b;
+        v[b] = 0.f;
+        if (q < T_ && xa + q < N)
+            v[b] = to_float(__ldg(ptr + base + (unsigned)((xa + q) * es)));
+    }
+}
+
+template <int NB>
+__device__ __forceinline__ void gather_tile_lines(float (&v)[NB], const Lines &img, int ln, int N, int xa, int q0,
+                                                  int T)
+{
+    const unsigned base = (unsigned)(ln * (int)img.line_step);
+    const int es = (int)img.elem_step;
+    if (img.dtype == DT_U8)
+        gather_tile_t<unsigned char, NB>(v, static_cast<const unsigned char *>(img.ptr), base, es, N, xa, q0, T);
+    else if (img.dtype == DT_F16)
+        gather_tile_t<__half, NB>(v, static_cast<const __half *>(img.ptr), base, es, N, xa, q0, T);
+    else
+        gather_tile_t<float, NB>(v, static_cast<const float *>(img.ptr), base, es, N, xa, q0, T);
+}
+
+template <int NB>
+__device__ __forceinline__ void scatter_padded(float *buf, const float (&v)[NB], int q0, int len)
+{
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int q = q0 + 32 * b;
+        if (q < len)
+            buf[pad_index(q)] = v[b];
+    }
+}
+
+// Most window samples one thread gathers (S <= kMaxS, K <= kMaxK), and most tile
+// positions (T <= 31 M).
+constexpr int kWindowSlots = (32 * kRun + kMaxS + 2 * kMaxK + 2 * kRun + 31) / 32;
+constexpr int kTileSlots = (31 * kRun + 31) / 32;
+
+// Window load of the distance kernel: buf(w)[pad_index(q)] = sample at position
+// pos0 + q of line line0 + w (reflected), q < len.
+__device__ __forceinline__ void load_windows(float *smem, int per_warp, const Lines &v, int n_lines,
+                                             int N, int line0, int pos0, int len)
+{
+    int w, q0;
+    gather_slot(v.elem_step == 1, w, q0);
+    const int ln = line0 + w;
+    if (ln >= n_lines)
+        return;
+    float val[kWindowSlots];
+    gather_window(val, v, ln, N, pos0, q0, len);
+    scatter_padded(smem + w * per_warp, val, q0, len);
+}
+
+// 1/x for x >= 1: the SFU estimate refined by one Newton-Raphson step
+// (e = 1 - x r, r' = r + r e), which roughly squares the relative error.
+__device__ __forceinline__ float rcp_nr(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+
+// One chunk of M search offsets s = c*M + sg, sg = 1..min(M, S - c*M), for the
+// lane's run. Every chunk runs the same code (one body, so that the warps of an
+// SM share one copy in the instruction cache); the last chunk of a pass may stop
+// early. Mirrored contributions wait in slot t = m + sg of a 2M-entry buffer
+// whose lower half belongs to lane r + c and upper half to lane r + c + 1, and
+// are delivered with warp shuffles at the end of the chunk.
+template <int K, int DM, bool SURE>
+__device__ __forceinline__ void nlm_chunk(const float *__restrict__ fl, int lane, int c, int lim,
+                                          const float (&fo)[kRun + 2 * K], float (&A)[kRun], float (&Q)[kRun],
+                                          float (&A2)[kRun], float c2, const float *__restrict__ g,
+                                          float *wK, int LW)
+{
+    constexpr int M = kRun;
+    constexpr int NF = M + 2 * K;
+    constexpr int NG = 2 * M + 2 * K;
+    // samples at positions x0 + c*M + 1 - K + j (lanes r + c and r + c + 1)
+    float gv[NG];
+    const float *gp = fl + 9 * (lane + c);
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+        gv[j] = gp[(1 + j) + (1 + j) / 8];
+    // slots 1..M are first written at sg = 1; the others may stay empty when the
+    // chunk stops early
+    float BA[2 * M], BQ[2 * M], BA2[2 * M];
+#pragma unroll
+    for (int t = M + 1; t < 2 * M; ++t)
+        BA[t] = BQ[t] = BA2[t] = 0.f;
+#pragma unroll
+    for (int sg = 1; sg <= M; ++sg) {
+        if (sg > lim)
+            break;
+        float dl[NF];
+#pragma unroll
+        for (int u = 0; u < NF; ++u)
+            dl[u] = gv[u + sg - 1] - fo[u];
+        float D[M];
+        patch_distances<K, DM, M>(dl, D, g);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float w = exp2_sfu(D[m] * c2);
+            const float d = dl[m + K];
+            const int t = m + sg;
+            const bool first = (t <= M) && (sg == 1);
+            A[m] = fmaf(w, d, A[m]);
+            Q[m] += w;
+            BA[t] = first ? -w * d : fmaf(-w, d, BA[t]);
+            BQ[t] = first ? w : BQ[t] + w;
+            if constexpr (SURE) {
+                const float v = w * d;
+                A2[m] = fmaf(v, d, A2[m]);
+                BA2[t] = first ? v * d : fmaf(v, d, BA2[t]);
+                if (sg <= K && c == 0)
+                    wK[(sg - 1) * LW + 9 * lane + m] = w;
+            }
+        }
+    }
+    // deliver the mirrored contributions
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const float ra = __shfl_up_sync(0xffffffffu, BA[M + j], c + 1);
+        const float rq = __shfl_up_sync(0xffffffffu, BQ[M + j], c + 1);
+        if (j > 0) {
+            A[j] += __shfl_up_sync(0xffffffffu, BA[j], c) + ra;
+            Q[j] += __shfl_up_sync(0xffffffffu, BQ[j], c) + rq;
+        } else {
+            A[j] += ra;
+            Q[j] += rq;
+        }
+        if constexpr (SURE) {
+            const float r2 = __shfl_up_sync(0xffffffffu, BA2[M + j], c + 1);
+            A2[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BA2[j], c) + r2 : r2;
+        }
+    }
+}
+
+// Offsets (in floats) of the per-warp rows of a pass's shared-memory layout: the
+// line window (reused for fhat), then blend | SURE: K weight rows, delta_in,
+// delta_out, f_rc, f. Tile rows are padded like the window (pad_index).
+struct RowOffsets {
+    int bl, wk, din, dout, rc, f;
+    __device__ __forceinline__ RowOffsets(const WarpLayout &L, int K)
+    {
+        bl = L.LF;
+        wk = bl + L.LT;
+        din = wk + K * L.LW;
+        dout = din + L.LT;
+        rc = dout + L.LT;
+        f = rc + L.LT;
+    }
+};
+
+__device__ __forceinline__ void st_global_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Store the M results of a lane to out[o + m], m < nvalid, with two 16-byte stores
+// when the run is whole and aligned.
+__device__ __forceinline__ void store_run(float *out, const float (&v)[kRun], int nvalid)
+{
+    if (nvalid == kRun && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        st_global_v4(out, v[0], v[1], v[2], v[3]);
+        st_global_v4(out + 4, v[4], v[5], v[6], v[7]);
     } else {
-        const int w = threadIdx.x % kWarpsPerCta;
-        const int ln = line0 + w;
-        float *buf = smem + w * per_warp + off;
-        const int es = (int)elem_step;
-        const float *col = img + (ln < n_lines ? ln * (int)line_step : 0);
-        for (int q = threadIdx.x / kWarpsPerCta; q < T; q += blockDim.x / kWarpsPerCta)
-            buf[q + (q >> 3)] = (ln < n_lines && xa + q < N) ? __ldg(col + (xa + q) * es) : fill;
+#pragma unroll
+        for (int m = 0; m < kRun; ++m)
+            if (m < nvalid)
+                out[m] = v[m];
+    }
+}
+
+// The end of a unit, after the search: finalise each lane's run in registers
+// (fhat = f + A/Q, optionally blended; for SURE the chained derivative of Eq. (24)
+// and the sums of its valid pixels), write the results (row-like outputs straight
+// from registers; column-like outputs through the warp's rows and 16-byte stores
+// across the CTA's 4 lines) and reduce the SURE sums of the unit into its record.
+// All threads of the CTA must call it. `pw` is the per-warp stride of smem (floats).
+template <int K, int DM, bool SURE>
+__device__ __forceinline__ void unit_epilogue(const PassArgs &p, float *smem, int pw, const RowOffsets &R, int LW,
+                                              int unit, int line0, int xa, int T, int HR, bool have_line,
+                                              const float (&fo)[kRun + 2 * K], const float (&A)[kRun],
+                                              const float (&Q)[kRun], const float (&A2)[kRun])
+{
+    constexpr int M = kRun;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int line = line0 + wid;
+    const int N = p.N;
+    const int qe = min(T, N - xa);                    // valid positions of the tile
+    const bool row_like = p.out_elem_step == 1;
+    const int ls = (int)p.out_line_step, es = (int)p.out_elem_step;
+    float *const fl = smem + wid * pw;
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (have_line && lane >= HR) {
+        const int j = lane - HR;
+        const int nvalid = min(M, qe - 8 * j);
+        const float *wf_row = fl + R.wk + 9 * lane;   // w(x, s) of the lane's own positions
+        const float ih2 = SURE ? __frcp_rn(p.h2) : 0.f;
+        float fh[M], dv[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float Qt = 1.f + Q[m];
+            const float r = rcp_nr(Qt);
+            const float mu = A[m] * r;
+            float v = fo[m + K] + mu;
+            if (p.blend)
+                v = 0.5f * (v + fl[R.bl + 9 * j + m]);
+            fh[m] = v;
+            dv[m] = 0.f;
+            if constexpr (SURE) {
+                // Eq. (24): the patch-overlap term over 0 < |s| <= min(K, S),
+                // T = sum_s g(s) [wf (a_s - mu) a_-s + wb (a_-s - mu) a_s] = TA - mu TB
+                // with a_s = f(x+s) - f(x), wf = w(x, s), wb = w(x-s, s). Position
+                // 8 lane + m - s of the padded weight row is at 9 lane + (m - s) - (m < s).
+                float TA = 0.f, TB = 0.f;
+#pragma unroll
+                for (int sg = 1; sg <= K; ++sg) {
+                    if (sg > p.S)
+                        break;
+                    const float ap = fo[m + K + sg] - fo[m + K];
+                    const float am = fo[m + K - sg] - fo[m + K];
+                    float wf = wf_row[(sg - 1) * LW + m];
+                    float wb = wf_row[(sg - 1) * LW + (m - sg) - (m < sg ? 1 : 0)];
+                    if constexpr (DM == DIST_FIR) {
+                        wf *= p.g[K + sg];
+                        wb *= p.g[K + sg];
+                    }
+                    TA = fmaf(wf + wb, ap * am, TA);
+                    TB = fmaf(wf, am, fmaf(wb, ap, TB));
+                }
+                const float Tt = fmaf(-mu, TB, TA);
+                const float var = A2[m] - mu * A[m];   // sum_j w (f(j) - fhat)^2
+                const float num = p.h2 + 2.f * Tt + 2.f * var;
+                dv[m] = fl[R.din + 9 * j + m] * (num * r) * ih2;
+                if (m < nvalid) {
+                    s[5] += dv[m];
+                    if (p.aux_rc.ptr) {
+                        // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
+                        const float rc = fl[R.rc + 9 * j + m];
+                        const float fv = fl[R.f + 9 * j + m];
+                        const float mm = 0.5f * (rc + v), dd = 0.5f * (rc - v);
+                        s[0] = fmaf(mm, mm, s[0]);
+                        s[1] = fmaf(mm, dd, s[1]);
+                        s[2] = fmaf(dd, dd, s[2]);
+                        s[3] = fmaf(fv, mm, s[3]);
+                        s[4] = fmaf(fv, dd, s[4]);
+                    }
+                }
+            }
+        }
+        if (row_like) {
+            if (nvalid > 0) {
+                const unsigned o = (unsigned)(line * ls + xa + 8 * j);
+                store_run(p.dst + o, fh, nvalid);
+                if (SURE && p.delta_out)
+                    store_run(p.delta_out + o, dv, nvalid);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                fl[9 * j + m] = fh[m];
+                if constexpr (SURE)
+                    fl[R.dout + 9 * j + m] = dv[m];
+            }
+        }
+    }
+    if (!row_like) {
+        // column-like output: position q of the CTA's lines line0..line0+3
+        __syncthreads();
+        const int nl = min(kWarpsPerCta, p.n_lines - line0);
+        const bool packed = ls == 1 && nl == kWarpsPerCta;
+        for (int q = threadIdx.x; q < qe; q += blockDim.x) {
+            const int pq = pad_index(q);
+            const unsigned o = (unsigned)(line0 * ls + (xa + q) * es);
+            float v[kWarpsPerCta], d[kWarpsPerCta];
+#pragma unroll
+            for (int w = 0; w < kWarpsPerCta; ++w) {
+                v[w] = smem[w * pw + pq];
+                d[w] = SURE ? smem[w * pw + R.dout + pq] : 0.f;
+            }
+            if (packed && (reinterpret_cast<uintptr_t>(p.dst + o) & 15) == 0) {
+                st_global_v4(p.dst + o, v[0], v[1], v[2], v[3]);
+                if (SURE && p.delta_out)
+                    st_global_v4(p.delta_out + o, d[0], d[1], d[2], d[3]);
+            } else {
+#pragma unroll
+                for (int w = 0; w < kWarpsPerCta; ++w)
+                    if (w < nl) {
+                        p.dst[o + w * ls] = v[w];
+                        if (SURE && p.delta_out)
+                            p.delta_out[o + w * ls] = d[w];
+                    }
+            }
+        }
+    }
+    if constexpr (SURE) {
+        if (p.partials) {
+            // deterministic reduction: float warp tree, then the warps in order in fp64
+            __shared__ float red[kWarpsPerCta][6];
+            const int k0 = p.aux_rc.ptr ? 0 : 5;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float v = k >= k0 ? s[k] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0)
+                    red[wid][k] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < kPartials) {
+                double t = 0.0;
+                if (threadIdx.x < 6)
+                    for (int w = 0; w < kWarpsPerCta; ++w)
+                        t += (double)red[w][threadIdx.x];
+                p.partials[(long long)unit * kPartials + threadIdx.x] = t;
+            }
+        }
     }
 }
 
@@ -200,213 +565,87 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
 {
     constexpr int M = kRun;
     constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
-    constexpr int NG = 2 * M + 2 * K;    // shifted samples needed for one chunk of M offsets
 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.S, N = p.N;
     const int HR = div_up(S, M), nch = div_up(S, M);
     const int T = tile_positions(S);
-    const int tiles = div_up(N, T);                // units are numbered tile fastest
-    const int xa = (bid % tiles) * T;
+    const int tiles = p.tiles;                     // units are numbered tile fastest
+    const int grp = bid / tiles;
+    const int xa = (bid - grp * tiles) * T;
     const int b0 = xa - HR * M;
-    const int line0 = (bid / tiles) * kWarpsPerCta;
+    const int line0 = grp * kWarpsPerCta;
     const int line = line0 + wid;
     const WarpLayout L = warp_layout(S, K, SURE, false);
-
+    const RowOffsets R(L, K);
     float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
-    float *const wK = fl + L.LF;                   // SURE: w(x, s) for s = 1..K (padded rows)
-    float *const din = wK + K * L.LW;              // SURE: delta_in of the tile
-    float *const dst_d = din + L.LT;               // SURE: delta_out of the tile
 
-    // ---- load: the line windows (with reflection) and delta_in
-    load_windows(smem, L.per_warp, p.src, p.n_lines, N, line0, b0 - K, 32 * M + nch * M + 2 * K + M);
-    if constexpr (SURE) {
-        if (p.delta_in)
-            load_tile(smem, L.per_warp, (int)(din - fl), p.delta_in, p.out_line_step, p.out_elem_step,
-                      p.n_lines, N, line0, xa, T, 1.f);
-        else
-            for (int q = lane; q < T; q += 32)
-                din[pad_index(q)] = 1.f;
+    // ---- load phase: the line windows (with reflection) and every tile input the
+    // epilogue reads, all gathered before the first shared-memory store
+    {
+        int w, q0;
+        gather_slot(p.src.elem_step == 1, w, q0);
+        const int ln = line0 + w;
+        const int len = 32 * M + nch * M + 2 * K + M;
+        float vw[kWindowSlots];
+        if (ln < p.n_lines)
+            gather_window(vw, p.src, ln, N, b0 - K, q0, len);
+        int ow, oq0;
+        gather_slot(p.out_elem_step == 1, ow, oq0);
+        const int oln = line0 + ow;
+        const bool oline = oln < p.n_lines;
+        float vb[kTileSlots], vd[kTileSlots], vr[kTileSlots], vf[kTileSlots];
+        if (p.blend && oline)
+            gather_tile(vb, p.blend, p.out_line_step, p.out_elem_step, oln, N, xa, oq0, T, 0.f);
+        if constexpr (SURE) {
+            if (oline) {
+                if (p.delta_in)
+                    gather_tile(vd, p.delta_in, p.out_line_step, p.out_elem_step, oln, N, xa, oq0, T, 1.f);
+                if (p.aux_rc.ptr) {
+                    gather_tile(vr, static_cast<const float *>(p.aux_rc.ptr), p.aux_rc.line_step,
+                                p.aux_rc.elem_step, oln, N, xa, oq0, T, 0.f);
+                    gather_tile_lines(vf, p.aux_f, oln, N, xa, oq0, T);
+                }
+            }
+        }
+        if (ln < p.n_lines)
+            scatter_padded(smem + w * L.per_warp, vw, q0, len);
+        float *const ob = smem + ow * L.per_warp;
+        if (p.blend && oline)
+            scatter_padded(ob + R.bl, vb, oq0, T);
+        if constexpr (SURE) {
+            if (p.delta_in && oline) {
+                scatter_padded(ob + R.din, vd, oq0, T);
+            } else {
+#pragma unroll
+                for (int b = 0; b < kTileSlots; ++b)
+                    if (oq0 + 32 * b < T)
+                        ob[R.din + pad_index(oq0 + 32 * b)] = 1.f;
+            }
+            if (p.aux_rc.ptr && oline) {
+                scatter_padded(ob + R.rc, vr, oq0, T);
+                scatter_padded(ob + R.f, vf, oq0, T);
+            }
+        }
     }
     __syncthreads();
 
-    if (line < p.n_lines) {
+    float fo[NF];
+    float A[M], Q[M], A2[M];
+    const bool have_line = line < p.n_lines;
+    if (have_line) {
         // samples of the own run with the patch halo: positions x0 - K + u
-        float fo[NF];
 #pragma unroll
         for (int u = 0; u < NF; ++u)
             fo[u] = fl[9 * lane + u + u / 8];
-        float A[M], Q[M], A2[M];
 #pragma unroll
         for (int m = 0; m < M; ++m)
             A[m] = Q[m] = A2[m] = 0.f;
-
-        for (int c = 0; c < nch; ++c) {
-            // samples at positions x0 + c*M + 1 - K + j (lanes r + c and r + c + 1)
-            float g[NG];
-            const float *gp = fl + 9 * (lane + c);
-#pragma unroll
-            for (int j = 0; j < NG; ++j)
-                g[j] = gp[(1 + j) + (1 + j) / 8];
-            // mirrored contributions: slot t goes to lane r + c (t < M) or r + c + 1
-            float BA[2 * M], BQ[2 * M], BA2[2 * M];
-#pragma unroll
-            for (int t = M + 1; t < 2 * M; ++t)
-                BA[t] = BQ[t] = BA2[t] = 0.f;
-            BA[0] = BQ[0] = BA2[0] = 0.f;
-#pragma unroll
-            for (int sg = 1; sg <= M; ++sg) {
-                if (c * M + sg > S)
-                    break;
-                float dl[NF];
-#pragma unroll
-                for (int u = 0; u < NF; ++u)
-                    dl[u] = g[u + sg - 1] - fo[u];
-                float D[M];
-                patch_distances<K, DM, M>(dl, D, p.g);
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const float w = exp2_sfu(D[m] * p.c2);
-                    const float d = dl[m + K];
-                    const int t = m + sg;
-                    const bool first = (sg == 1);   // slots 1..M are first written at sg = 1
-                    A[m] = fmaf(w, d, A[m]);
-                    BA[t] = first ? -w * d : fmaf(-w, d, BA[t]);
-                    if constexpr (SURE) {
-                        const float v = w * d;
-                        A2[m] = fmaf(v, d, A2[m]);
-                        BA2[t] = first ? v * d : fmaf(v, d, BA2[t]);
-                        if (c == 0 && sg <= K)
-                            wK[(sg - 1) * L.LW + 9 * lane + m] = w;
-                    }
-                    Q[m] += w;
-                    BQ[t] = first ? w : BQ[t] + w;
-                }
-            }
-            // deliver the mirrored contributions
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                const float ra = __shfl_up_sync(0xffffffffu, BA[M + j], c + 1);
-                const float rq = __shfl_up_sync(0xffffffffu, BQ[M + j], c + 1);
-                if (j > 0) {
-                    A[j] += __shfl_up_sync(0xffffffffu, BA[j], c) + ra;
-                    Q[j] += __shfl_up_sync(0xffffffffu, BQ[j], c) + rq;
-                } else {
-                    A[j] += ra;
-                    Q[j] += rq;
-                }
-                if constexpr (SURE) {
-                    const float r2 = __shfl_up_sync(0xffffffffu, BA2[M + j], c + 1);
-                    A2[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BA2[j], c) + r2 : r2;
-                }
-            }
-        }
+        for (int c = 0; c < nch; ++c)
+            nlm_chunk<K, DM, SURE>(fl, lane, c, S - c * M, fo, A, Q, A2, p.c2, p.g, fl + R.wk, L.LW);
         __syncwarp();
-
-        // ---- finalise own pixels: fhat = f + A/Q (and the chained derivative)
-        if (lane >= HR) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const int q = 9 * (lane - HR) + m;          // padded tile index
-                const float Qt = 1.f + Q[m];
-                const float mu = __fdiv_rn(A[m], Qt);
-                fl[q] = fo[m + K] + mu;
-                if constexpr (SURE) {
-                    // Eq. (24): the patch-overlap term over 0 < |s| <= min(K, S),
-                    // T = sum_s g(s) [wf (a_s - mu) a_-s + wb (a_-s - mu) a_s] = TA - mu TB
-                    // with a_s = f(x+s) - f(x), wf = w(x, s), wb = w(x-s, s).
-                    float TA = 0.f, TB = 0.f;
-#pragma unroll
-                    for (int sg = 1; sg <= K; ++sg) {
-                        if (sg > S)
-                            break;
-                        const float ap = fo[m + K + sg] - fo[m + K];
-                        const float am = fo[m + K - sg] - fo[m + K];
-                        float wf = wK[(sg - 1) * L.LW + 9 * lane + m];
-                        const int pb = 8 * lane + m - sg;   // position of x - s, >= 0
-                        float wb = wK[(sg - 1) * L.LW + pb + (pb >> 3)];
-                        if constexpr (DM == DIST_FIR) {
-                            wf *= p.g[K + sg];
-                            wb *= p.g[K + sg];
-                        }
-                        TA = fmaf(wf + wb, ap * am, TA);
-                        TB = fmaf(wf, am, fmaf(wb, ap, TB));
-                    }
-                    const float Tt = fmaf(-mu, TB, TA);
-                    const float var = A2[m] - mu * A[m];   // sum_j w (f(j) - fhat)^2
-                    const float num = p.h2 + 2.f * Tt + 2.f * var;
-                    dst_d[q] = din[q] * __fdiv_rn(num, Qt * p.h2);
-                }
-            }
-        }
     }
-    __syncthreads();
-
-    // ---- store: fhat (optionally blended), delta_out, partial sums
-    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    {
-        const bool row_like = p.out_elem_step == 1;
-        const int w = row_like ? wid : (int)(threadIdx.x % kWarpsPerCta);
-        const int q0 = row_like ? lane : (int)(threadIdx.x / kWarpsPerCta);
-        const int qs = row_like ? 32 : (int)(blockDim.x / kWarpsPerCta);
-        const int ln = line0 + w;
-        const float *wb = smem + w * L.per_warp;
-        const int qe = (ln < p.n_lines) ? min(T, N - xa) : 0;
-        const int ls = (int)p.out_line_step, es = (int)p.out_elem_step;
-        for (int q = q0; q < qe; q += qs) {
-            const int x = xa + q;
-            const unsigned o = (unsigned)(ln * ls + x * es);
-            float v = wb[q + (q >> 3)];
-            if (p.blend)
-                v = 0.5f * (v + __ldg(p.blend + o));
-            p.dst[o] = v;
-            if constexpr (SURE) {
-                const float dv = wb[(int)(dst_d - fl) + q + (q >> 3)];
-                if (p.delta_out)
-                    p.delta_out[o] = dv;
-                s[5] += dv;
-                if (p.aux_rc.ptr) {
-                    // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
-                    const float rc = load_sample(p.aux_rc, ln, x);
-                    const float fv = load_sample(p.aux_f, ln, x);
-                    const float mm = 0.5f * (rc + v), dd = 0.5f * (rc - v);
-                    s[0] = fmaf(mm, mm, s[0]);
-                    s[1] = fmaf(mm, dd, s[1]);
-                    s[2] = fmaf(dd, dd, s[2]);
-                    s[3] = fmaf(fv, mm, s[3]);
-                    s[4] = fmaf(fv, dd, s[4]);
-                }
-            }
-        }
-    }
-    if constexpr (SURE) {
-        if (p.partials) {
-            // deterministic reduction: float warp tree, then the warps in order in fp64
-            const int nk = p.aux_rc.ptr ? 6 : 1;
-            __shared__ float red[kWarpsPerCta][6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                if (k >= 6 - nk) {
-                    float v = s[k];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-                        v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0)
-                        red[wid][k] = v;
-                } else if (lane == 0) {
-                    red[wid][k] = 0.f;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < kPartials) {
-                double t = 0.0;
-                if (threadIdx.x < 6)
-                    for (int w = 0; w < kWarpsPerCta; ++w)
-                        t += (double)red[w][threadIdx.x];
-                p.partials[(long long)bid * kPartials + threadIdx.x] = t;
-            }
-        }
-    }
+    unit_epilogue<K, DM, SURE>(p, smem, L.per_warp, R, L.LW, bid, line0, xa, T, HR, have_line, fo, A, Q, A2);
 }
 
 template <int K, int DM, bool SURE>
