@@ -78,17 +78,25 @@ __device__ bool wait_count(const int *ctr, int need, unsigned long long limit_ns
     return true;
 }
 
+// Each pass variant is its own (not inlined) function, so that its registers are
+// allocated for it alone rather than for the union of six inlined bodies.
+template <int K, int DM, bool SURE>
+__device__ __noinline__ void pass_unit_variant(const PassArgs &a, int unit, float *smem)
+{
+    process_tile<K, DM, SURE>(a, unit, smem);
+}
+
 template <int K>
 __device__ __forceinline__ void run_pass_unit(const BatchJob &j, int unit, float *smem)
 {
     const int sel = j.dm * 2 + j.sure;
     switch (sel) {
-    case DIST_SLIDE * 2 + 0: process_tile<K, DIST_SLIDE, false>(j.a, unit, smem); break;
-    case DIST_SLIDE * 2 + 1: process_tile<K, DIST_SLIDE, true>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 0: process_tile<K, DIST_BLOCK, false>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 1: process_tile<K, DIST_BLOCK, true>(j.a, unit, smem); break;
-    case DIST_FIR * 2 + 0: process_tile<K, DIST_FIR, false>(j.a, unit, smem); break;
-    default: process_tile<K, DIST_FIR, true>(j.a, unit, smem); break;
+    case DIST_SLIDE * 2 + 0: pass_unit_variant<K, DIST_SLIDE, false>(j.a, unit, smem); break;
+    case DIST_SLIDE * 2 + 1: pass_unit_variant<K, DIST_SLIDE, true>(j.a, unit, smem); break;
+    case DIST_BLOCK * 2 + 0: pass_unit_variant<K, DIST_BLOCK, false>(j.a, unit, smem); break;
+    case DIST_BLOCK * 2 + 1: pass_unit_variant<K, DIST_BLOCK, true>(j.a, unit, smem); break;
+    case DIST_FIR * 2 + 0: pass_unit_variant<K, DIST_FIR, false>(j.a, unit, smem); break;
+    default: pass_unit_variant<K, DIST_FIR, true>(j.a, unit, smem); break;
     }
 }
 
