@@ -75,6 +75,52 @@ __device__ __forceinline__ float exp2_sfu(float x)
     return y;
 }
 
+// Two floats in one 64-bit register pair (lo, hi) for the packed FP32x2 forms of
+// FFMA/FMUL (sm_100 and later): one issue slot for two lane-operations.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f32x2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float f32x2_lo(f32x2 v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+
+__device__ __forceinline__ float f32x2_hi(f32x2 v)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+
+__device__ __forceinline__ f32x2 f32x2_fma(f32x2 a, f32x2 b, f32x2 c)   // a * b + c, each half rounded once
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 f32x2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 f32x2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Patch distances D[m] = sum_{k=-K..K} g(k) * dl[m + K + k]^2 for m = 0..M-1,
 // where dl holds the lifted differences of M + 2K consecutive positions.
 template <int K, int DM, int M>
@@ -100,13 +146,26 @@ __device__ __forceinline__ void patch_distances(const float (&dl)[M + 2 * K], fl
         for (int u = U + 1; u < M + 2 * K; ++u)
             pre[u] = fmaf(dl[u], dl[u], pre[u - 1]);
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            if (m >= U)
-                D[m] = pre[m + 2 * K];
-            else if (m + 2 * K < U)
-                D[m] = suf[m];
-            else
-                D[m] = suf[m] + pre[m + 2 * K];
+        for (int m = 0; m < M; m += 2) {
+            const bool both0 = m < U && m + 2 * K >= U, both1 = m + 1 < U && m + 1 + 2 * K >= U;
+            if (both0 && both1) {
+                // two windows that are both suffix + prefix: one packed add
+                const f32x2 r = f32x2_add(f32x2_pack(suf[m], suf[m + 1]),
+                                          f32x2_pack(pre[m + 2 * K], pre[m + 1 + 2 * K]));
+                D[m] = f32x2_lo(r);
+                D[m + 1] = f32x2_hi(r);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int mm = m + e;
+                    if (mm >= U)
+                        D[mm] = pre[mm + 2 * K];
+                    else if (mm + 2 * K < U)
+                        D[mm] = suf[mm];
+                    else
+                        D[mm] = suf[mm] + pre[mm + 2 * K];
+                }
+            }
         }
     } else if constexpr (DM == DIST_SLIDE) {
         // Running sum (box profile): two updates per step, whatever K is.
@@ -302,7 +361,9 @@ __device__ __forceinline__ float rcp_nr(float x)
 // SM share one copy in the instruction cache); the last chunk of a pass may stop
 // early. Mirrored contributions wait in slot t = m + sg of a 2M-entry buffer
 // whose lower half belongs to lane r + c and upper half to lane r + c + 1, and
-// are delivered with warp shuffles at the end of the chunk.
+// are delivered with warp shuffles at the end of the chunk. The SURE form keeps
+// (A, A2) and the mirrored (-A, A2) contributions as float pairs: both take
+// (w, w d) x d, one packed FMA each.
 template <int K, int DM, bool SURE>
 __device__ __forceinline__ void nlm_chunk(const float *__restrict__ fl, int lane, int c, int lim,
                                           const float (&fo)[kRun + 2 * K], float (&A)[kRun], float (&Q)[kRun],
@@ -320,10 +381,21 @@ __device__ __forceinline__ void nlm_chunk(const float *__restrict__ fl, int lane
         gv[j] = gp[(1 + j) + (1 + j) / 8];
     // slots 1..M are first written at sg = 1; the others may stay empty when the
     // chunk stops early
-    float BA[2 * M], BQ[2 * M], BA2[2 * M];
+    float BA[2 * M], BQ[2 * M];
+    f32x2 AA[M], BB[2 * M];             // SURE: (A, A2) and mirrored (-A, A2)
+    if constexpr (SURE) {
 #pragma unroll
-    for (int t = M + 1; t < 2 * M; ++t)
-        BA[t] = BQ[t] = BA2[t] = 0.f;
+        for (int m = 0; m < M; ++m)
+            AA[m] = f32x2_pack(A[m], A2[m]);
+    }
+#pragma unroll
+    for (int t = M + 1; t < 2 * M; ++t) {
+        BQ[t] = 0.f;
+        if constexpr (SURE)
+            BB[t] = 0ull;
+        else
+            BA[t] = 0.f;
+    }
 #pragma unroll
     for (int sg = 1; sg <= M; ++sg) {
         if (sg > lim)
@@ -334,40 +406,59 @@ __device__ __forceinline__ void nlm_chunk(const float *__restrict__ fl, int lane
             dl[u] = gv[u + sg - 1] - fo[u];
         float D[M];
         patch_distances<K, DM, M>(dl, D, g);
+        float X[M];                     // exponents d^2 * c2, two per packed multiply
+#pragma unroll
+        for (int m = 0; m < M; m += 2) {
+            const f32x2 x = f32x2_mul(f32x2_pack(D[m], D[m + 1]), f32x2_pack(c2, c2));
+            X[m] = f32x2_lo(x);
+            X[m + 1] = f32x2_hi(x);
+        }
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const float w = exp2_sfu(D[m] * c2);
+            const float w = exp2_sfu(X[m]);
             const float d = dl[m + K];
             const int t = m + sg;
             const bool first = (t <= M) && (sg == 1);
-            A[m] = fmaf(w, d, A[m]);
             Q[m] += w;
-            BA[t] = first ? -w * d : fmaf(-w, d, BA[t]);
             BQ[t] = first ? w : BQ[t] + w;
             if constexpr (SURE) {
-                const float v = w * d;
-                A2[m] = fmaf(v, d, A2[m]);
-                BA2[t] = first ? v * d : fmaf(v, d, BA2[t]);
+                const f32x2 wv = f32x2_pack(w, w * d);
+                const f32x2 dd = f32x2_pack(d, d);
+                AA[m] = f32x2_fma(wv, dd, AA[m]);
+                BB[t] = first ? f32x2_mul(wv, dd) : f32x2_fma(wv, dd, BB[t]);
                 if (sg <= K && c == 0)
                     wK[(sg - 1) * LW + 9 * lane + m] = w;
+            } else {
+                A[m] = fmaf(w, d, A[m]);
+                BA[t] = first ? -w * d : fmaf(-w, d, BA[t]);
             }
         }
     }
     // deliver the mirrored contributions
+    const f32x2 sgn = f32x2_pack(-1.f, 1.f);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-        const float ra = __shfl_up_sync(0xffffffffu, BA[M + j], c + 1);
         const float rq = __shfl_up_sync(0xffffffffu, BQ[M + j], c + 1);
-        if (j > 0) {
-            A[j] += __shfl_up_sync(0xffffffffu, BA[j], c) + ra;
-            Q[j] += __shfl_up_sync(0xffffffffu, BQ[j], c) + rq;
-        } else {
-            A[j] += ra;
-            Q[j] += rq;
-        }
+        Q[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BQ[j], c) + rq : rq;
         if constexpr (SURE) {
-            const float r2 = __shfl_up_sync(0xffffffffu, BA2[M + j], c + 1);
-            A2[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BA2[j], c) + r2 : r2;
+            const float n1 = __shfl_up_sync(0xffffffffu, f32x2_lo(BB[M + j]), c + 1);
+            const float s1 = __shfl_up_sync(0xffffffffu, f32x2_hi(BB[M + j]), c + 1);
+            AA[j] = f32x2_fma(f32x2_pack(n1, s1), sgn, AA[j]);
+            if (j > 0) {
+                const float n0 = __shfl_up_sync(0xffffffffu, f32x2_lo(BB[j]), c);
+                const float s0 = __shfl_up_sync(0xffffffffu, f32x2_hi(BB[j]), c);
+                AA[j] = f32x2_fma(f32x2_pack(n0, s0), sgn, AA[j]);
+            }
+        } else {
+            const float ra = __shfl_up_sync(0xffffffffu, BA[M + j], c + 1);
+            A[j] += (j > 0) ? __shfl_up_sync(0xffffffffu, BA[j], c) + ra : ra;
+        }
+    }
+    if constexpr (SURE) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            A[m] = f32x2_lo(AA[m]);
+            A2[m] = f32x2_hi(AA[m]);
         }
     }
 }
@@ -648,8 +739,14 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
     unit_epilogue<K, DM, SURE>(p, smem, L.per_warp, R, L.LW, bid, line0, xa, T, HR, have_line, fo, A, Q, A2);
 }
 
+// CTAs per SM the compiler is held to (registers per thread = 65536 / (128 x this)),
+// chosen per variant by measurement on GB300: the plain running-sum pass is fastest
+// at 5 (96 registers), the float and SURE passes at 4 (128 registers, no spills).
+template <int DM, bool SURE>
+constexpr int pass_min_ctas() { return (SURE || DM != DIST_SLIDE) ? 4 : 5; }
+
 template <int K, int DM, bool SURE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, SURE ? 4 : 5) nlm_pass_kernel(const __grid_constant__ PassArgs p)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<DM, SURE>()) nlm_pass_kernel(const __grid_constant__ PassArgs p)
 {
     extern __shared__ __align__(16) float smem[];
     process_tile<K, DM, SURE>(p, (int)blockIdx.x, smem);
