@@ -258,6 +258,77 @@ int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records);
 const char *snlm_kernel_name(int kind);
 
 /*
+ * Serving loop (no counterpart in the paper): continuous batching of requests
+ * that arrive over time. Submit requests whose images and result buffers are in
+ * HOST memory (pinned memory lets the copies overlap), each with an arrival time
+ * in seconds on the server's clock (which starts at the first snlm_server_drain),
+ * then drain: the calling thread runs the loop until every submitted request is
+ * served, and returns.
+ *
+ * SNLM_SERVE_BATCHED: requests are admitted from a FIFO queue as device memory
+ * (a slab of mem_budget bytes allocated at creation; <= 0: half the free memory)
+ * and one of `streams` streams free up. A request of at least solo_pixels pixels,
+ * or a lone request on an idle GPU, runs alone through the per-image path; the
+ * consecutive smaller requests at the front of the queue (at most max_batch) run
+ * as one batch plan (the persistent launch of snlm_batch_plan_*). Each launch
+ * copies its inputs in, runs, and copies its results out on its own stream, so
+ * launches overlap on the device. SNLM_SERVE_PLAIN serves one request at a time
+ * through the per-image path and waits for each (the per-request baseline).
+ * Results are those of snlm_denoise (bitwise for RC/CR/AVG; SURE within the float
+ * rounding of its sums).
+ */
+typedef enum { SNLM_SERVE_BATCHED = 0, SNLM_SERVE_PLAIN = 1 } snlm_serve_mode;
+
+typedef struct {
+    const void *img;   /* HOST input, H rows of `pitch` elements of `dtype` */
+    float *out;        /* HOST output, H*W float32 */
+    int dtype, H, W, pitch;
+    int S, K;
+    float h;
+    int profile, order;
+    float sigma, beta; /* as in snlm_denoise */
+    double t_arrival;  /* seconds on the server clock, >= 0 */
+} snlm_serve_request;
+
+typedef struct {
+    int mode;               /* snlm_serve_mode */
+    long long mem_budget;   /* device bytes for admitted requests; <= 0: half the free memory */
+    int streams;            /* launches in flight (1..64; plain mode uses 1) */
+    int max_batch;          /* requests per batch launch */
+    long long solo_pixels;  /* requests of at least this many pixels run alone */
+    int ctas_per_sm;        /* batch kernels; <= 0: as many as fit */
+} snlm_server_config;
+
+typedef struct {
+    int launches;             /* solo and batch launches made */
+    int max_batch;            /* most requests in one launch */
+    int max_inflight;         /* most launches in flight at once */
+    int images;               /* requests served */
+    long long max_used_bytes; /* peak of the admitted requests' device memory */
+    long long budget_bytes;   /* the slab */
+    double wall_s;            /* server clock at the end of the last drain */
+    double host_busy_s;       /* time the loop spent not sleeping */
+} snlm_server_stats;
+
+typedef struct snlm_server snlm_server;
+
+/* cfg may be NULL (defaults: batched, half the free memory, 4 streams, 256 per batch,
+ * 1<<20 solo pixels). SNLM_ERR_NOMEM if the slab cannot be allocated. */
+int snlm_server_create(const snlm_server_config *cfg, snlm_server **server);
+/* Validates and queues n requests (host pointers stay owned by the caller and must
+ * stay valid until the drain that serves them returns); ids[i] (may be NULL)
+ * receives each request's id. SNLM_ERR_NOMEM for a request larger than the slab. */
+int snlm_server_submit(snlm_server *server, const snlm_serve_request *reqs, int n, int *ids);
+/* Runs the loop until every submitted request has its result in host memory. */
+int snlm_server_drain(snlm_server *server);
+/* Completion time (server clock, -1 if not served yet) and launch index of a request. */
+int snlm_server_result(const snlm_server *server, int id, double *t_done, int *launch);
+int snlm_server_get_stats(const snlm_server *server, snlm_server_stats *stats);
+double snlm_server_clock(const snlm_server *server);
+/* Waits for work in flight and frees the slab and streams. */
+void snlm_server_destroy(snlm_server *server);
+
+/*
  * Process-wide options (no counterpart in the paper).
  *
  * SNLM_OPT_TMA (default 0): 1 makes the per-image passes (snlm_denoise*, SURE

@@ -35,6 +35,27 @@ class BatchConfig(ctypes.Structure):
                 ("spin_limit_us", ctypes.c_int), ("fail_job", ctypes.c_int)]
 
 
+class ServeRequest(ctypes.Structure):
+    """snlm_serve_request of include/snlm.h."""
+    _fields_ = [("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("S", ctypes.c_int),
+                ("K", ctypes.c_int), ("h", ctypes.c_float), ("profile", ctypes.c_int), ("order", ctypes.c_int),
+                ("sigma", ctypes.c_float), ("beta", ctypes.c_float), ("t_arrival", ctypes.c_double)]
+
+
+class ServerConfig(ctypes.Structure):
+    """snlm_server_config of include/snlm.h."""
+    _fields_ = [("mode", ctypes.c_int), ("mem_budget", ctypes.c_longlong), ("streams", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("solo_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    """snlm_server_stats of include/snlm.h."""
+    _fields_ = [("launches", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("images", ctypes.c_int), ("max_used_bytes", ctypes.c_longlong),
+                ("budget_bytes", ctypes.c_longlong), ("wall_s", ctypes.c_double), ("host_busy_s", ctypes.c_double)]
+
+
 def load(build_if_missing: bool = False):
     """Load libsnlm.so (optionally building it first). Raises LibraryMissing."""
     global _lib
@@ -101,6 +122,20 @@ def load(build_if_missing: bool = False):
         lib.snlm_get_option.restype = ctypes.c_longlong
         lib.snlm_device_error.argtypes = [vp]
         lib.snlm_device_error.restype = ci
+        lib.snlm_server_create.argtypes = [ctypes.POINTER(ServerConfig), pp]
+        lib.snlm_server_create.restype = ci
+        lib.snlm_server_submit.argtypes = [vp, ctypes.POINTER(ServeRequest), ci, ctypes.POINTER(ci)]
+        lib.snlm_server_submit.restype = ci
+        lib.snlm_server_drain.argtypes = [vp]
+        lib.snlm_server_drain.restype = ci
+        lib.snlm_server_result.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ci)]
+        lib.snlm_server_result.restype = ci
+        lib.snlm_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.snlm_server_get_stats.restype = ci
+        lib.snlm_server_clock.argtypes = [vp]
+        lib.snlm_server_clock.restype = ctypes.c_double
+        lib.snlm_server_destroy.argtypes = [vp]
+        lib.snlm_server_destroy.restype = None
         del fp, dp
         _lib = lib
         return lib
@@ -113,5 +148,6 @@ EXPORTED = [
     "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc", "snlm_batch_plan_create",
     "snlm_batch_plan_workspace_bytes", "snlm_batch_plan_upload", "snlm_batch_plan_launch",
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
-    "snlm_set_option", "snlm_get_option", "snlm_device_error",
+    "snlm_set_option", "snlm_get_option", "snlm_device_error", "snlm_server_create", "snlm_server_submit",
+    "snlm_server_drain", "snlm_server_result", "snlm_server_get_stats", "snlm_server_clock", "snlm_server_destroy",
 ]

@@ -316,3 +316,64 @@ def snlm_batch_plan_info(plan):
 
 def snlm_batch_plan_destroy(plan):
     _lib.load().snlm_batch_plan_destroy(ctypes.c_void_p(plan))
+
+
+# ------------------------------------------------------------------ serving loop
+
+SERVE_BATCHED, SERVE_PLAIN = 0, 1
+
+
+def snlm_server_create(mode: int = SERVE_BATCHED, mem_budget: int = 0, streams: int = 4, max_batch: int = 256,
+                       solo_pixels: int = 1 << 20, ctas_per_sm: int = 0):
+    """Create a serving loop (see include/snlm.h); returns its handle."""
+    lib = _lib.load()
+    cfg = _lib.ServerConfig(int(mode), int(mem_budget), int(streams), int(max_batch), int(solo_pixels),
+                            int(ctas_per_sm))
+    h = ctypes.c_void_p()
+    _check(lib.snlm_server_create(ctypes.byref(cfg), ctypes.byref(h)), "snlm_server_create")
+    return h.value
+
+
+def snlm_server_submit(server, requests):
+    """Queue requests: dicts with img and out (pinned CPU tensors), S, K, h,
+    profile, order, sigma, beta, t_arrival. Returns their ids."""
+    lib = _lib.load()
+    n = len(requests)
+    arr = (_lib.ServeRequest * n)()
+    for i, r in enumerate(requests):
+        dt, H, W, pitch = _image_args(r["img"])
+        arr[i] = _lib.ServeRequest(r["img"].data_ptr(), r["out"].data_ptr(), dt, H, W, pitch, int(r["S"]),
+                                   int(r["K"]), float(r["h"]), _profile(r.get("profile", "box")),
+                                   _order(r.get("order", "RC")), float(r.get("sigma") or 0.0),
+                                   float(r.get("beta") or 0.0), float(r["t_arrival"]))
+    ids = (ctypes.c_int * max(n, 1))()
+    _check(lib.snlm_server_submit(ctypes.c_void_p(server), arr, n, ids), "snlm_server_submit")
+    return [ids[i] for i in range(n)]
+
+
+def snlm_server_drain(server):
+    _check(_lib.load().snlm_server_drain(ctypes.c_void_p(server)), "snlm_server_drain")
+
+
+def snlm_server_result(server, rid: int):
+    """(completion time on the server clock, launch index) of a request."""
+    t, k = ctypes.c_double(), ctypes.c_int()
+    _check(_lib.load().snlm_server_result(ctypes.c_void_p(server), int(rid), ctypes.byref(t), ctypes.byref(k)),
+           "snlm_server_result")
+    return t.value, k.value
+
+
+def snlm_server_get_stats(server) -> dict:
+    st = _lib.ServerStats()
+    _check(_lib.load().snlm_server_get_stats(ctypes.c_void_p(server), ctypes.byref(st)), "snlm_server_get_stats")
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def snlm_server_clock(server) -> float:
+    return float(_lib.load().snlm_server_clock(ctypes.c_void_p(server)))
+
+
+def snlm_server_destroy(server):
+    if server:
+        _lib.load().snlm_server_destroy(ctypes.c_void_p(server))
+

@@ -88,15 +88,15 @@ __device__ __forceinline__ f32x2 f32x2_pack(float lo, float hi)
 
 __device__ __forceinline__ float f32x2_lo(f32x2 v)
 {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    float lo;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(lo) : "l"(v));
     return lo;
 }
 
 __device__ __forceinline__ float f32x2_hi(f32x2 v)
 {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    float hi;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(hi) : "l"(v));
     return hi;
 }
 

@@ -5,16 +5,19 @@ A request carries its own image (host memory), S, K, h, profile and order. The
 server replays an arrival schedule against the wall clock and loops:
 
 1. admission: arrived requests are admitted in arrival order while their device
-   footprint (input, output, their share of batch scratch) fits the memory budget
-   (a fraction of the free HBM when the server starts, or an explicit cap); the
-   input is copied host-to-device on an upload stream;
-2. step: all admitted requests not yet launched become one batch plan (the native
-   persistent launch over their tile units), launched on one of `streams`
-   rotating streams after their uploads; a step may start while earlier steps are
-   still running, so requests that arrive during a step overlap with it on the GPU;
-3. retirement: a finished step's outputs are copied back to pinned host buffers,
-   its memory is released and each request's latency (arrival to result in host
-   memory) is recorded.
+   footprint (input, output, their scratch) fits the memory budget (a fraction of
+   the free HBM when the server starts, or an explicit cap); the input is copied
+   host-to-device on an upload stream;
+2. launch: admitted requests of at least `solo_pixels` pixels run alone through the
+   per-image path (they fill the GPU by themselves), each on its own stream with its
+   own workspace; the smaller ones become one batch plan (the native persistent
+   launch over their tile units) — or run alone too when one small request finds
+   the GPU idle, which keeps the latency of a quiet server at the per-image path's.
+   Up to `streams` launches are in flight, so work that arrives meanwhile overlaps
+   with them on the GPU;
+3. retirement: every finished launch (in completion order) has its outputs copied
+   back to pinned host buffers, its memory released and each request's latency
+   (arrival to result in host memory) recorded.
 
 The plain path serves the same schedule one request at a time with
 snlm_denoise_host-style calls (copy in, denoise, copy out).
@@ -140,8 +143,8 @@ class ServeStats:
 class Server:
     """The continuous-batching loop (single host thread)."""
 
-    def __init__(self, device=None, mem_budget: int | None = None, mem_fraction: float = 0.5, streams: int = 3,
-                 max_batch: int = 256, ctas_per_sm: int = 0):
+    def __init__(self, device=None, mem_budget: int | None = None, mem_fraction: float = 0.5, streams: int = 4,
+                 max_batch: int = 256, ctas_per_sm: int = 0, solo_pixels: int = 1024 * 1024):
         import torch
 
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
@@ -151,20 +154,48 @@ class Server:
         self.upload = torch.cuda.Stream(self.dev)
         self.max_batch = max_batch
         self.ctas_per_sm = ctas_per_sm
+        self.solo_pixels = solo_pixels
 
-    def run(self, schedule, stats: ServeStats | None = None):
+    def _launch_solo(self, item, st):
+        import torch
+
+        r, d_in, d_out, ev, _ = item
+        st.wait_event(ev)
+        with torch.cuda.stream(st):
+            ws = torch.empty(api.snlm_workspace_bytes(r.shape[0], r.shape[1], r.order), dtype=torch.uint8,
+                             device=self.dev)
+            api.snlm_denoise_ws(d_in, r.S, r.K, r.h, r.profile, r.order, r.sigma, r.beta, out=d_out, workspace=ws,
+                                stream=st)
+            done = torch.cuda.Event()
+            done.record(st)
+        return {"batch": None, "keep": ws, "done": done, "members": [item], "stream": st}
+
+    def _launch_batch(self, items, st):
         import torch
 
         from .batch import Batch
+
+        for (_, _, _, ev, _) in items:
+            st.wait_event(ev)
+        reqs = [dict(img=d_in, out=d_out, S=r.S, K=r.K, h=r.h, profile=r.profile, order=r.order,
+                     sigma=r.sigma, beta=r.beta) for (r, d_in, d_out, _, _) in items]
+        with torch.cuda.stream(st):
+            b = Batch(reqs, ctas_per_sm=self.ctas_per_sm, stream=st)
+            b.run(st)
+            done = torch.cuda.Event()
+            done.record(st)
+        return {"batch": b, "keep": None, "done": done, "members": items, "stream": st}
+
+    def run(self, schedule, stats: ServeStats | None = None):
+        import torch
 
         stats = stats or ServeStats()
         prepare_outputs(schedule)
         pending = list(schedule)          # in arrival order
         pi = 0
-        admitted = []                     # (req, dev_in, dev_out, event)
-        inflight = []                     # (batch, event, [(req, dev_in, dev_out)], bytes)
+        admitted = []                     # (req, dev_in, dev_out, upload event, bytes)
+        inflight = []                     # launches: dicts of _launch_solo / _launch_batch
         used = 0
-        nstream = 0
         t0 = time.perf_counter()
         while pi < len(pending) or admitted or inflight:
             now = time.perf_counter() - t0
@@ -188,44 +219,58 @@ class Server:
                 pi += 1
             h1 = time.perf_counter()
             stats.host_s["admit"] += h1 - h0
-            # 2. launch a step over everything admitted
-            if admitted and len(inflight) < len(self.streams):
-                st = self.streams[nstream % len(self.streams)]
-                nstream += 1
-                for (_, _, _, ev, _) in admitted:
-                    st.wait_event(ev)
-                reqs = [dict(img=d_in, out=d_out, S=r.S, K=r.K, h=r.h, profile=r.profile, order=r.order,
-                             sigma=r.sigma, beta=r.beta) for (r, d_in, d_out, _, _) in admitted]
-                with torch.cuda.stream(st):
-                    b = Batch(reqs, ctas_per_sm=self.ctas_per_sm, stream=st)
-                    b.run(st)
-                    done = torch.cuda.Event()
-                    done.record(st)
-                for (r, _, _, _, _) in admitted:
-                    r.step = stats.steps
-                inflight.append((b, done, admitted, st))
-                stats.steps += 1
-                stats.max_batch = max(stats.max_batch, len(admitted))
+            # 2. launches on the free streams: large requests alone, the rest batched
+            if admitted:
+                busy = {id(e["stream"]) for e in inflight}
+                free_streams = [st for st in self.streams if id(st) not in busy]
+                large = [a for a in admitted if a[0].shape[0] * a[0].shape[1] >= self.solo_pixels]
+                small = [a for a in admitted if a[0].shape[0] * a[0].shape[1] < self.solo_pixels]
+                if len(small) == 1 and not inflight and not large:
+                    large, small = small, []          # a lone request on an idle GPU
+                launched = []
+
+                def start(e):
+                    for (r, _, _, _, _) in e["members"]:
+                        r.step = stats.steps
+                    stats.steps += 1
+                    stats.max_batch = max(stats.max_batch, len(e["members"]))
+                    inflight.append(e)
+                    launched.extend(e["members"])
+
+                for a in large:
+                    if not free_streams:
+                        break
+                    start(self._launch_solo(a, free_streams.pop(0)))
+                if small and free_streams:
+                    start(self._launch_batch(small, free_streams.pop(0)))
+                if launched:
+                    ids = {id(a) for a in launched}
+                    admitted = [a for a in admitted if id(a) not in ids]
                 stats.max_inflight = max(stats.max_inflight, len(inflight))
-                admitted = []
             h2 = time.perf_counter()
             stats.host_s["launch"] += h2 - h1
-            # 3. retire finished steps (in launch order)
-            while inflight and inflight[0][1].query():
-                b, done, members, st = inflight.pop(0)
-                if b.status(st) != api.OK:
+            # 3. retire every finished launch
+            keep = []
+            for e in inflight:
+                if not e["done"].query():
+                    keep.append(e)
+                    continue
+                st = e["stream"]
+                if e["batch"] is not None and e["batch"].status(st) != api.OK:
                     raise RuntimeError("a batch step reported a timed-out dependency wait")
                 with torch.cuda.stream(st):
-                    for (r, d_in, d_out, _, need) in members:
+                    for (r, d_in, d_out, _, need) in e["members"]:
                         r.out.copy_(d_out, non_blocking=True)
                 st.synchronize()
                 t_done = time.perf_counter() - t0
-                for (r, d_in, d_out, _, need) in members:
+                for (r, d_in, d_out, _, need) in e["members"]:
                     r.t_done = t_done
                     stats.latencies.append(r.latency())
                     used -= need
-                stats.images += len(members)
-                b.close()
+                stats.images += len(e["members"])
+                if e["batch"] is not None:
+                    e["batch"].close()
+            inflight = keep
             stats.host_s["retire"] += time.perf_counter() - h2
             if pi < len(pending) and not admitted and not inflight:
                 # idle until the next arrival
@@ -260,3 +305,43 @@ def run_plain(schedule, device=None, stats: ServeStats | None = None):
         stats.images += 1
     stats.wall = time.perf_counter() - t0
     return stats
+
+
+
+class NativeServer:
+    """The library's own serving loop (snlm_server_* of include/snlm.h): the same
+    admission, solo/batch launches over rotating streams and retirement as
+    `Server`, run in C++ by the calling thread. mode "batched" is continuous
+    batching; "plain" serves one request at a time through the per-image path (the
+    per-request baseline, with the same host-side cost per request)."""
+
+    def __init__(self, mode: str = "batched", mem_budget: int | None = None, streams: int = 4,
+                 max_batch: int = 256, solo_pixels: int = 1024 * 1024, ctas_per_sm: int = 0):
+        import torch
+
+        self.mode = {"batched": 0, "plain": 1}[mode]
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            mem_budget = min(free // 2, 16 << 30)
+        self.cfg = (self.mode, int(mem_budget), int(streams), int(max_batch), int(solo_pixels), int(ctas_per_sm))
+
+    def run(self, schedule, stats: ServeStats | None = None):
+        stats = stats or ServeStats()
+        prepare_outputs(schedule)
+        mode, budget, streams, max_batch, solo, ctas = self.cfg
+        handle = api.snlm_server_create(mode, budget, streams, max_batch, solo, ctas)
+        try:
+            ids = api.snlm_server_submit(handle, [dict(img=r.img, out=r.out, S=r.S, K=r.K, h=r.h, profile=r.profile,
+                                                       order=r.order, sigma=r.sigma, beta=r.beta,
+                                                       t_arrival=r.t_arrival) for r in schedule])
+            api.snlm_server_drain(handle)
+            for i, r in zip(ids, schedule):
+                r.t_done, r.step = api.snlm_server_result(handle, i)
+                stats.latencies.append(r.latency())
+            st = api.snlm_server_get_stats(handle)
+            stats.images, stats.steps, stats.max_batch = st["images"], st["launches"], st["max_batch"]
+            stats.max_inflight, stats.max_used, stats.wall = st["max_inflight"], st["max_used_bytes"], st["wall_s"]
+            stats.host_s = {"loop": st["host_busy_s"]}
+        finally:
+            api.snlm_server_destroy(handle)
+        return stats

@@ -1,6 +1,8 @@
-"""The continuous-batching service: schedule generation (CPU), and on the GPU the
-result of every request alone equals its result in the mix, admission under a
-memory cap, and rejection of a request larger than the whole budget."""
+"""The continuous-batching service (the Python loop `Server` and the library's own
+loop `NativeServer`): schedule generation (CPU), and on the GPU the result of every
+request alone equals its result in the mix, launches overlap, admission under a
+memory cap, the plain (one request at a time) mode, and rejection of a request
+larger than the whole budget."""
 import math
 
 import numpy as np
@@ -81,3 +83,53 @@ def test_admission_under_a_memory_cap(dev):
     with pytest.raises(ValueError):
         serve.Server(dev, mem_budget=1024).run(big)
     assert api.snlm_version() >= 100
+
+
+@pytest.mark.gpu
+def test_native_server_results_alone_equal_results_in_the_mix(dev):
+    reqs = serve.make_schedule(48, rate=6000.0, seed=7, sizes=(128, 256, 512, 1024), weights=(0.4, 0.3, 0.2, 0.1))
+    stats = serve.NativeServer("batched").run(reqs)
+    assert stats.images == len(reqs)
+    assert stats.max_batch > 1                         # small requests shared launches
+    assert stats.max_inflight > 1                      # launches overlapped on the device
+    for r in reqs:
+        ref = alone(r, dev)
+        got = r.out.numpy()
+        if r.order == "SURE":
+            assert np.abs(got - ref).max() <= TOL
+        else:
+            assert np.array_equal(got, ref), (r.rid, r.order)
+        assert r.t_done >= r.t_arrival
+    s = stats.summary()
+    assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+@pytest.mark.gpu
+def test_native_plain_mode_serves_one_at_a_time(dev):
+    reqs = serve.make_schedule(10, rate=1e6, seed=8, sizes=(128, 256), weights=(0.5, 0.5))
+    stats = serve.NativeServer("plain").run(reqs)
+    assert stats.images == 10 and stats.max_batch == 1 and stats.max_inflight == 1
+    for r in reqs[:4]:
+        ref = alone(r, dev)
+        tol = TOL if r.order == "SURE" else 0.0
+        assert np.abs(r.out.numpy() - ref).max() <= tol
+
+
+@pytest.mark.gpu
+def test_native_server_admission_under_a_memory_cap(dev):
+    from paper_1407_2343_gb300 import api
+
+    reqs = serve.make_schedule(12, rate=1e6, seed=2, sizes=(256,), weights=(1.0,))
+    cap = max(serve._footprint(r) for r in reqs) * 3
+    stats = serve.NativeServer("batched", mem_budget=cap).run(reqs)
+    assert stats.images == 12
+    assert 0 < stats.max_used <= cap
+    assert stats.steps >= 3                            # memory forced several launches
+    for r in reqs[:4]:
+        ref = alone(r, dev)
+        tol = TOL if r.order == "SURE" else 0.0
+        assert np.abs(r.out.numpy() - ref).max() <= tol
+    big = serve.make_schedule(1, rate=1.0, seed=4, sizes=(512,), weights=(1.0,))
+    with pytest.raises(api.SnlmError) as e:
+        serve.NativeServer("batched", mem_budget=1 << 20).run(big)
+    assert e.value.status == api.ERR_NOMEM
