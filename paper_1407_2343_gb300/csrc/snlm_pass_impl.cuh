@@ -332,6 +332,219 @@ __device__ __forceinline__ void scatter_padded(float *buf, const float (&v)[NB],
 constexpr int kWindowSlots = (32 * kRun + kMaxS + 2 * kMaxK + 2 * kRun + 31) / 32;
 constexpr int kTileSlots = (31 * kRun + 31) / 32;
 
+// Vector forms of the window and tile loads (16-byte and narrower aligned loads)
+// for the common layouts; each returns false, having loaded nothing, when its
+// conditions do not hold, and the scalar gathers above run instead. Every load of
+// a form is issued before the first shared-memory store.
+
+__device__ __forceinline__ float byte_of(unsigned v, int e) { return (float)((v >> (8 * e)) & 0xffu); }
+
+// Row-like window of line `ln`, positions ws .. ws+len-1 all inside [0, N):
+// float samples in 16-byte vectors, 8-bit samples in 16-byte vectors of 16.
+__device__ __forceinline__ bool load_window_row_vec(float *buf, const Lines &v, int ln, int N, int ws, int len,
+                                                    int lane)
+{
+    if (v.dtype == DT_F32) {
+        const float *row = static_cast<const float *>(v.ptr) + ln * (int)v.line_step;
+        const int a = ws & ~3, off = ws - a, nv = (off + len + 3) >> 2;
+        if (a < 0 || a + 4 * nv > N || (reinterpret_cast<uintptr_t>(row + a) & 15) != 0)
+            return false;
+        const float4 *src = reinterpret_cast<const float4 *>(row + a);
+        constexpr int J = (kWindowSlots * 32 + 127) / 128 + 1;   // float4 per lane, at most
+        float4 r[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (lane + 32 * j < nv)
+                r[j] = __ldg(src + lane + 32 * j);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            if (k < nv) {
+                const float e4[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = 4 * k + e - off;
+                    if (q >= 0 && q < len)
+                        buf[pad_index(q)] = e4[e];
+                }
+            }
+        }
+        return true;
+    }
+    if (v.dtype == DT_U8) {
+        const unsigned char *row = static_cast<const unsigned char *>(v.ptr) + ln * (int)v.line_step;
+        const int a = ws & ~15, off = ws - a, nv = (off + len + 15) >> 4;
+        if (a < 0 || a + 16 * nv > N || (reinterpret_cast<uintptr_t>(row + a) & 15) != 0)
+            return false;
+        const uint4 *src = reinterpret_cast<const uint4 *>(row + a);
+        constexpr int J = (kWindowSlots * 32 + 511) / 512 + 1;
+        uint4 r[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (lane + 32 * j < nv)
+                r[j] = __ldg(src + lane + 32 * j);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            if (k < nv) {
+                const unsigned w4[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int q = 16 * k + e - off;
+                    if (q >= 0 && q < len)
+                        buf[pad_index(q)] = byte_of(w4[e >> 2], e & 3);
+                }
+            }
+        }
+        return true;
+    }
+    return false;
+}
+
+// Column-like window of the CTA's 4 lines (adjacent in memory): one load brings the
+// 4 samples of a position (16 bytes of float, 8 of half, 4 of 8-bit samples).
+__device__ __forceinline__ bool load_window_col_vec(float *smem, int per_warp, const Lines &v, int n_lines, int N,
+                                                    int line0, int ws, int len)
+{
+    const int es = v.dtype == DT_U8 ? 1 : (v.dtype == DT_F16 ? 2 : 4);
+    if (v.line_step != 1 || line0 + kWarpsPerCta > n_lines || (v.elem_step & 3) != 0 ||
+        (reinterpret_cast<uintptr_t>(v.ptr) & (uintptr_t)(4 * es - 1)) != 0)
+        return false;
+    constexpr int J = (kWindowSlots * 32 + 4 * 32 * kWarpsPerCta - 1) / (32 * kWarpsPerCta);
+    const int es_step = (int)v.elem_step;
+    if (v.dtype == DT_F32) {
+        const float *base = static_cast<const float *>(v.ptr) + line0;
+        float4 r[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = threadIdx.x + blockDim.x * j;
+            if (q < len)
+                r[j] = __ldg(reinterpret_cast<const float4 *>(base + reflect_index(ws + q, N) * es_step));
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = threadIdx.x + blockDim.x * j;
+            if (q < len) {
+                const int pq = pad_index(q);
+                smem[pq] = r[j].x;
+                smem[per_warp + pq] = r[j].y;
+                smem[2 * per_warp + pq] = r[j].z;
+                smem[3 * per_warp + pq] = r[j].w;
+            }
+        }
+        return true;
+    }
+    if (v.dtype == DT_U8) {
+        const unsigned char *base = static_cast<const unsigned char *>(v.ptr) + line0;
+        unsigned r[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = threadIdx.x + blockDim.x * j;
+            if (q < len)
+                r[j] = __ldg(reinterpret_cast<const unsigned *>(base + reflect_index(ws + q, N) * es_step));
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = threadIdx.x + blockDim.x * j;
+            if (q < len) {
+                const int pq = pad_index(q);
+#pragma unroll
+                for (int w = 0; w < kWarpsPerCta; ++w)
+                    smem[w * per_warp + pq] = byte_of(r[j], w);
+            }
+        }
+        return true;
+    }
+    const __half *base = static_cast<const __half *>(v.ptr) + line0;
+    uint2 r[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int q = threadIdx.x + blockDim.x * j;
+        if (q < len)
+            r[j] = __ldg(reinterpret_cast<const uint2 *>(base + reflect_index(ws + q, N) * es_step));
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int q = threadIdx.x + blockDim.x * j;
+        if (q < len) {
+            const int pq = pad_index(q);
+            const __half2 lo = *reinterpret_cast<const __half2 *>(&r[j].x);
+            const __half2 hi = *reinterpret_cast<const __half2 *>(&r[j].y);
+            smem[pq] = __low2float(lo);
+            smem[per_warp + pq] = __high2float(lo);
+            smem[2 * per_warp + pq] = __low2float(hi);
+            smem[3 * per_warp + pq] = __high2float(hi);
+        }
+    }
+    return true;
+}
+
+// A float tile input (positions xa .. xa+T-1 of the CTA's lines, `fill` past N)
+// into the padded rows at float offset `row` of each warp. Row-like views: 16-byte
+// vectors along each line; column-like views: the 4 lines of a position in one
+// 16-byte load. False (nothing loaded) when the layout does not allow it.
+__device__ __forceinline__ bool load_tile_vec(float *smem, int per_warp, int row, const float *img,
+                                              long long line_step, long long elem_step, int n_lines, int N,
+                                              int line0, int xa, int T, float fill)
+{
+    const int qe = min(T, N - xa);                      // valid positions
+    if (elem_step == 1) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int ln = line0 + w;
+        const float *src = img + (ln < n_lines ? ln * (int)line_step : 0) + xa;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) != 0 || (line_step & 3) != 0)
+            return false;
+        float *buf = smem + w * per_warp + row;
+        constexpr int J = (32 * kRun + 127) / 128;      // float4 per lane (T <= 31 * 8)
+        float4 r[J];
+        const int nv = qe >> 2;                         // whole vectors inside the line
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (ln < n_lines && lane + 32 * j < nv)
+                r[j] = __ldg(reinterpret_cast<const float4 *>(src) + lane + 32 * j);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            if (4 * k < T) {
+                const bool whole = ln < n_lines && k < nv;
+                const float e4[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = 4 * k + e;
+                    if (q < T)
+                        buf[pad_index(q)] = whole ? e4[e] : (ln < n_lines && q < qe ? __ldg(src + q) : fill);
+                }
+            }
+        }
+        return true;
+    }
+    if (line_step != 1 || line0 + kWarpsPerCta > n_lines || (elem_step & 3) != 0 ||
+        (reinterpret_cast<uintptr_t>(img + line0) & 15) != 0)
+        return false;
+    constexpr int J = (32 * kRun + 32 * kWarpsPerCta - 1) / (32 * kWarpsPerCta);
+    float4 r[J];
+    const int es = (int)elem_step;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int q = threadIdx.x + blockDim.x * j;
+        if (q < qe)
+            r[j] = __ldg(reinterpret_cast<const float4 *>(img + line0 + (xa + q) * es));
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int q = threadIdx.x + blockDim.x * j;
+        if (q < T) {
+            const int pq = row + pad_index(q);
+            const bool ok = q < qe;
+            smem[pq] = ok ? r[j].x : fill;
+            smem[per_warp + pq] = ok ? r[j].y : fill;
+            smem[2 * per_warp + pq] = ok ? r[j].z : fill;
+            smem[3 * per_warp + pq] = ok ? r[j].w : fill;
+        }
+    }
+    return true;
+}
+
 // Window load of the distance kernel: buf(w)[pad_index(q)] = sample at position
 // pos0 + q of line line0 + w (reflected), q < len.
 __device__ __forceinline__ void load_windows(float *smem, int per_warp, const Lines &v, int n_lines,
@@ -672,49 +885,68 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
     float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
 
     // ---- load phase: the line windows (with reflection) and every tile input the
-    // epilogue reads, all gathered before the first shared-memory store
+    // epilogue reads. The vector forms serve the common layouts; the scalar gathers
+    // (every read issued before the first shared-memory store) serve the rest.
     {
+        const int len = 32 * M + nch * M + 2 * K + M;
+        const int ws = b0 - K;
+        // (the vector forms serve the plain passes: measured on GB300 they are slower
+        // for the SURE passes, whose several tile inputs then load in separate rounds)
+        bool done_win = false, vb_ok = false;
+        const bool vd_ok = false, vr_ok = false;
+        if constexpr (!SURE) {
+            if (p.src.elem_step == 1) {
+                done_win = line >= p.n_lines ||
+                           load_window_row_vec(smem + wid * L.per_warp, p.src, line, N, ws, len, lane);
+                done_win = __syncthreads_and(done_win);
+            } else {
+                done_win = load_window_col_vec(smem, L.per_warp, p.src, p.n_lines, N, line0, ws, len);
+            }
+            vb_ok = p.blend && load_tile_vec(smem, L.per_warp, R.bl, p.blend, p.out_line_step, p.out_elem_step,
+                                             p.n_lines, N, line0, xa, T, 0.f);
+        }
         int w, q0;
         gather_slot(p.src.elem_step == 1, w, q0);
         const int ln = line0 + w;
-        const int len = 32 * M + nch * M + 2 * K + M;
         float vw[kWindowSlots];
-        if (ln < p.n_lines)
-            gather_window(vw, p.src, ln, N, b0 - K, q0, len);
+        if (!done_win && ln < p.n_lines)
+            gather_window(vw, p.src, ln, N, ws, q0, len);
         int ow, oq0;
         gather_slot(p.out_elem_step == 1, ow, oq0);
         const int oln = line0 + ow;
         const bool oline = oln < p.n_lines;
         float vb[kTileSlots], vd[kTileSlots], vr[kTileSlots], vf[kTileSlots];
-        if (p.blend && oline)
+        if (p.blend && !vb_ok && oline)
             gather_tile(vb, p.blend, p.out_line_step, p.out_elem_step, oln, N, xa, oq0, T, 0.f);
         if constexpr (SURE) {
             if (oline) {
-                if (p.delta_in)
+                if (p.delta_in && !vd_ok)
                     gather_tile(vd, p.delta_in, p.out_line_step, p.out_elem_step, oln, N, xa, oq0, T, 1.f);
                 if (p.aux_rc.ptr) {
-                    gather_tile(vr, static_cast<const float *>(p.aux_rc.ptr), p.aux_rc.line_step,
-                                p.aux_rc.elem_step, oln, N, xa, oq0, T, 0.f);
+                    if (!vr_ok)
+                        gather_tile(vr, static_cast<const float *>(p.aux_rc.ptr), p.aux_rc.line_step,
+                                    p.aux_rc.elem_step, oln, N, xa, oq0, T, 0.f);
                     gather_tile_lines(vf, p.aux_f, oln, N, xa, oq0, T);
                 }
             }
         }
-        if (ln < p.n_lines)
+        if (!done_win && ln < p.n_lines)
             scatter_padded(smem + w * L.per_warp, vw, q0, len);
         float *const ob = smem + ow * L.per_warp;
-        if (p.blend && oline)
+        if (p.blend && !vb_ok && oline)
             scatter_padded(ob + R.bl, vb, oq0, T);
         if constexpr (SURE) {
-            if (p.delta_in && oline) {
-                scatter_padded(ob + R.din, vd, oq0, T);
-            } else {
+            if (!p.delta_in) {
 #pragma unroll
                 for (int b = 0; b < kTileSlots; ++b)
                     if (oq0 + 32 * b < T)
                         ob[R.din + pad_index(oq0 + 32 * b)] = 1.f;
+            } else if (!vd_ok && oline) {
+                scatter_padded(ob + R.din, vd, oq0, T);
             }
             if (p.aux_rc.ptr && oline) {
-                scatter_padded(ob + R.rc, vr, oq0, T);
+                if (!vr_ok)
+                    scatter_padded(ob + R.rc, vr, oq0, T);
                 scatter_padded(ob + R.f, vf, oq0, T);
             }
         }
