@@ -42,9 +42,14 @@ SFU_PEAK_TEXP = SMS * 32 * MAX_MHZ * 1e6 / 1e12
 # differences of both pixels, 2 more. One MUFU ex2 per unique pair.
 OPS_PER_PAIR = {"plain": 9, "sure": 11}
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
-# for the kernel sources whose hash is recorded with it (see profiles/).
-TRAFFIC = {"sources_sha": None, "kernel": None, "bytes_per_launch": None}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# pass kernels of the 4096^2 u8 SURE step, from one ncu --set full capture of
+# `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
+# --no-cpu-baseline --no-rc` (the first timed step's four passes); valid only while
+# the kernel sources hash to `sources_sha` (profiles/ has the capture's summary).
+TRAFFIC = {"sources_sha": "92c72d01d9ff3c96",
+           "bytes_per_launch": {"row_pass_sure/slide": 90.581248e6, "col_pass_sure/block": 179.153408e6,
+                                "col_pass_sure/slide": 96.090624e6, "row_pass_sure/block": 268.020224e6}}
 
 
 def kernel_sources_sha() -> str:
@@ -399,8 +404,9 @@ def run_ours(a):
     pairs_launch = px * a.S
     achieved = OPS_PER_PAIR[kind] * pairs_launch / avg_s / 1e12
     traffic = None
-    if TRAFFIC["sources_sha"] == kernel_sources_sha() and TRAFFIC["kernel"] == dom:
-        traffic = TRAFFIC["bytes_per_launch"]
+    if TRAFFIC["sources_sha"] == kernel_sources_sha() and a.size == 4096 and a.S == 20 and a.K == 5 and \
+            a.dtype == "u8" and a.profile == "box":
+        traffic = TRAFFIC["bytes_per_launch"].get(dom)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ALU_PEAK_TOPS,
                 "unit": "Tops/s (FP32 lane-ops)", "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
                 "ops_per_unique_pair": OPS_PER_PAIR[kind], "unique_pairs_per_launch": pairs_launch,
