@@ -52,6 +52,25 @@ TRAFFIC = {"sources_sha": "92c72d01d9ff3c96",
                                 "col_pass_sure/slide": 96.090624e6, "row_pass_sure/block": 268.020224e6}}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks of the process group (a job takes as long as its
+    slowest rank); x itself with one rank. `device` holds the reduction tensor: the
+    rank's CUDA device under NCCL, the CPU under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_2343_gb300", "csrc")
@@ -380,12 +399,9 @@ def run_ours(a):
         return dev_ms, wall, trace, ck
 
     dev_ms, wall, trace, clocks = timed(a.order, a.steps, Clocks(local))
-    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    dev_ms_max = float(t_max.item())
+    dev_ms_max = max_over_ranks(dev_ms, world, dev)
     px = H * W
-    value = world * a.steps * px / (dev_ms_max * 1e-3) / 1e6
+    value = job_rate(world, a.steps * px, dev_ms_max * 1e-3) / 1e6
     npass = passes_of(a.order)
     pairs_paper = world * a.steps * npass * px * (2 * a.S + 1) / (dev_ms_max * 1e-3)
 
@@ -424,9 +440,10 @@ def run_ours(a):
             "gpu_launches": len(trace), "clocks": clocks}
 
     if not a.no_rc and a.order != "RC":
-        ms_rc, _, tr_rc, _ = timed("RC", max(20, a.steps // 4))
         n_rc = max(20, a.steps // 4)
-        line["rc_order"] = {"Mpixel_s": world * n_rc * px / (ms_rc * 1e-3) / 1e6, "ms_per_step": ms_rc / n_rc,
+        ms_rc, _, tr_rc, _ = timed("RC", n_rc)
+        ms_rc = max_over_ranks(ms_rc, world, dev)
+        line["rc_order"] = {"Mpixel_s": job_rate(world, n_rc * px, ms_rc * 1e-3) / 1e6, "ms_per_step": ms_rc / n_rc,
                             "gpu_launches": len(tr_rc)}
 
     if not a.no_e2e:
@@ -440,10 +457,8 @@ def run_ours(a):
         for _ in range(n_e2e):
             api.snlm_denoise_host(host_in, a.S, a.K, h, a.profile, a.order, a.sigma, out=host_out, stream=stream)
         t_e2e = time.perf_counter() - t0
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        line["e2e"] = {"value": world * n_e2e * px / float(t.item()) / 1e6, "unit": "Mpixel/s",
+        t_e2e = max_over_ranks(t_e2e, world, dev)
+        line["e2e"] = {"value": job_rate(world, n_e2e * px, t_e2e) / 1e6, "unit": "Mpixel/s",
                        "h2d_bytes_per_step": int(img_np.nbytes), "d2h_bytes_per_step": int(H * W * 4),
                        "steps": n_e2e, "api": "snlm_denoise_host (pinned host buffers)"}
 
