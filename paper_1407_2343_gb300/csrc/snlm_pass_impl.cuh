@@ -114,6 +114,13 @@ __device__ __forceinline__ f32x2 f32x2_add(f32x2 a, f32x2 b)
     return d;
 }
 
+__device__ __forceinline__ f32x2 f32x2_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ f32x2 f32x2_mul(f32x2 a, f32x2 b)
 {
     f32x2 d;
@@ -613,10 +620,22 @@ __device__ __forceinline__ void nlm_chunk(const float *__restrict__ fl, int lane
     for (int sg = 1; sg <= M; ++sg) {
         if (sg > lim)
             break;
+        // the lift; in the plain passes, for odd sg, two positions per packed subtraction
+        // (the sample pairs (gv[2i], gv[2i+1]) against (fo[u], fo[u+1]), u even). The
+        // SURE passes keep the scalar form: the pairing constraints cost them spills.
         float dl[NF];
+        if (!SURE && (sg & 1)) {
 #pragma unroll
-        for (int u = 0; u < NF; ++u)
-            dl[u] = gv[u + sg - 1] - fo[u];
+            for (int u = 0; u < NF; u += 2) {
+                const f32x2 r = f32x2_sub(f32x2_pack(gv[u + sg - 1], gv[u + sg]), f32x2_pack(fo[u], fo[u + 1]));
+                dl[u] = f32x2_lo(r);
+                dl[u + 1] = f32x2_hi(r);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < NF; ++u)
+                dl[u] = gv[u + sg - 1] - fo[u];
+        }
         float D[M];
         patch_distances<K, DM, M>(dl, D, g);
         float X[M];                     // exponents d^2 * c2, two per packed multiply
