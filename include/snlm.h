@@ -117,6 +117,22 @@ int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, 
                       void *stream);
 
 /*
+ * Pipelined end-to-end variant for n same-shaped HOST images: image i is copied
+ * from imgs_host[i], denoised and copied into outs_host[i] (H*W float32) exactly
+ * as snlm_denoise_host would do it, but the copies run on two streams of the
+ * call's own, overlapped with the computation of the neighbouring images (two
+ * device input and two output buffers; the computations run one after another
+ * on `stream`). Returns after every result is in its buffer. The overlap needs
+ * pinned host memory; pageable memory works without it. Device buffers come from
+ * the library's pool. Arguments are validated as in snlm_denoise_host, plus:
+ * n >= 0 (n == 0 does nothing) and every imgs_host[i] and outs_host[i] non-NULL.
+ * Results are identical to n calls of snlm_denoise_host.
+ */
+int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host, int n, int dtype, int H,
+                           int W, int pitch, int S, int K, float h, int profile, int order, float sigma,
+                           float beta, void *stream);
+
+/*
  * One 1-D NLM pass (Eq. (4)) over n_lines signals, with the derivative chain of
  * Eq. (24) when delta_out is given (the computation of Alg. 3).
  *   x          DEVICE, samples of type dtype; sample i of line l is at

@@ -161,6 +161,57 @@ def snlm_denoise_host(img: np.ndarray, S: int, K: int, h: float | None = None, p
     return out
 
 
+def snlm_denoise_host_many(imgs, S: int, K: int, h: float | None = None, profile="box", order="RC",
+                           sigma: float | None = None, beta: float = 0.0, outs=None, stream=None):
+    """Pipelined end-to-end call on a sequence of same-shaped HOST images (numpy
+    arrays or CPU tensors, pinned for the overlap): each is copied in, denoised and
+    copied out as by snlm_denoise_host, with the copies overlapped with the
+    neighbours' computation. Returns the list of outputs (float32, H x W)."""
+    torch = _torch()
+    imgs = list(imgs)
+    if not imgs:
+        return []
+    codes = {np.dtype(np.uint8): U8, np.dtype(np.float16): F16, np.dtype(np.float32): F32}
+    keep, ptrs, shape = [], [], None
+    for im in imgs:
+        if isinstance(im, np.ndarray):
+            if im.ndim != 2 or im.dtype not in codes:
+                raise TypeError("images must be 2-D uint8/float16/float32 arrays")
+            a = np.ascontiguousarray(im)
+            args = (codes[a.dtype], a.shape[0], a.shape[1], a.shape[1])
+            ptrs.append(a.ctypes.data)
+            keep.append(a)
+        else:
+            args = _image_args(im)
+            ptrs.append(_ptr(im).value)
+            keep.append(im)
+        if shape is None:
+            shape = args
+        elif args != shape:
+            raise ValueError("all images must have the same dtype, shape and pitch")
+    dt, H, W, pitch = shape
+    h = _h_for(h, sigma, K, profile, beta)
+    if outs is None:
+        outs = [np.empty((H, W), np.float32) for _ in imgs]
+    if len(outs) != len(imgs):
+        raise ValueError("one output per image")
+    for o in outs:
+        ok = o.shape == (H, W) and (o.dtype == np.float32 and o.flags.c_contiguous if isinstance(o, np.ndarray)
+                                    else o.dtype == torch.float32 and o.is_contiguous() and o.device.type == "cpu")
+        if not ok:
+            raise ValueError("outputs must be contiguous float32 host arrays of shape (H, W)")
+    optrs = [o.ctypes.data if isinstance(o, np.ndarray) else _ptr(o).value for o in outs]
+    n = len(imgs)
+    iarr = (ctypes.c_void_p * n)(*ptrs)
+    oarr = (ctypes.c_void_p * n)(*optrs)
+    rc = _lib.load().snlm_denoise_host_many(iarr, oarr, n, dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                            _order(order), float(sigma or 0.0), float(beta or 0.0),
+                                            _stream_ptr(stream) if torch.cuda.is_available() else None)
+    del keep
+    _check(rc, "snlm_denoise_host_many")
+    return outs
+
+
 def snlm_nlm_1d(x, S: int, K: int, h: float, profile="box", beta: float = 0.0, fhat=None,
                 delta_in=None, delta_out=None, stream=None):
     """One 1-D NLM pass (Eq. (4)) over the rows of a 2-D device tensor `x`

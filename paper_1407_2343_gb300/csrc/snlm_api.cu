@@ -109,7 +109,8 @@ Pool &pool()
 }
 
 // Returns scratch of at least `need` bytes on the current device, slot `slot`
-// (0: denoise scratch, 1: host-call input, 2: host-call output).
+// (0: denoise scratch, 1 and 3: host-call inputs, 2 and 4: host-call outputs).
+constexpr int kPoolSlots = 5;
 void *pool_get(size_t need, int slot)
 {
     int dev = 0;
@@ -117,7 +118,7 @@ void *pool_get(size_t need, int slot)
         return nullptr;
     Pool &p = pool();
     std::lock_guard<std::mutex> g(p.mu);
-    const size_t idx = (size_t)dev * 3 + slot;
+    const size_t idx = (size_t)dev * kPoolSlots + slot;
     if (p.ptr.size() <= idx) {
         p.ptr.resize(idx + 1, nullptr);
         p.bytes.resize(idx + 1, 0);
@@ -372,6 +373,96 @@ int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, 
     if (e != cudaSuccess)
         return status_of(e);
     rc = status_of(cudaStreamSynchronize(st));
+    if (rc != SNLM_OK)
+        return rc;
+    return snlm_device_error(st);
+}
+
+int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host, int n, int dtype, int H,
+                           int W, int pitch, int S, int K, float h, int profile, int order, float sigma,
+                           float beta, void *stream)
+{
+    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (n < 0 || (n > 0 && (!imgs_host || !outs_host)) || !valid_dtype(dtype) || pitch < W ||
+        (long long)H * pitch >= (1LL << 31))
+        return SNLM_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!imgs_host[i] || !outs_host[i])
+            return SNLM_ERR_ARG;
+    if (n == 0)
+        return SNLM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t in_bytes = (size_t)H * pitch * dtype_size(dtype);
+    const size_t out_bytes = (size_t)H * W * sizeof(float);
+    void *din[2] = {pool_get(in_bytes, 1), pool_get(in_bytes, 3)};
+    void *dout[2] = {pool_get(out_bytes, 2), pool_get(out_bytes, 4)};
+    void *ws = pool_get(ws_layout(H, W, S, order).total, 0);
+    if (!din[0] || !din[1] || !dout[0] || !dout[1] || !ws)
+        return SNLM_ERR_NOMEM;
+    // copies in on `cin`, computation on `st`, copies out on `cout`; buffer b = i & 1
+    // is reused by image i + 2 once image i's computation (input) and copy out
+    // (output) are done. Every wait names the latest record of its event.
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&in_done[b], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&comp_done[b], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&out_done[b], cudaEventDisableTiming);
+    }
+    rc = status_of(e);
+    for (int i = 0; i < n && rc == SNLM_OK; ++i) {
+        const int b = i & 1;
+        if (i >= 2)
+            e = cudaStreamWaitEvent(cin, comp_done[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(din[b], imgs_host[i], in_bytes, cudaMemcpyHostToDevice, cin);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(in_done[b], cin);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(st, in_done[b], 0);
+        if (e == cudaSuccess && i >= 2)
+            e = cudaStreamWaitEvent(st, out_done[b], 0);
+        rc = status_of(e);
+        if (rc != SNLM_OK)
+            break;
+        rc = denoise_core(din[b], dtype, H, W, pitch, S, K, h, profile, order, sigma, beta,
+                          static_cast<float *>(dout[b]), ws, nullptr, st);
+        if (rc != SNLM_OK)
+            break;
+        e = cudaEventRecord(comp_done[b], st);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(cout, comp_done[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(outs_host[i], dout[b], out_bytes, cudaMemcpyDeviceToHost, cout);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(out_done[b], cout);
+        rc = status_of(e);
+    }
+    // drain all three streams whatever happened, then release the call's objects
+    const int r1 = cin ? status_of(cudaStreamSynchronize(cin)) : SNLM_OK;
+    const int r2 = status_of(cudaStreamSynchronize(st));
+    const int r3 = cout ? status_of(cudaStreamSynchronize(cout)) : SNLM_OK;
+    for (int b = 0; b < 2; ++b) {
+        if (in_done[b])
+            cudaEventDestroy(in_done[b]);
+        if (comp_done[b])
+            cudaEventDestroy(comp_done[b]);
+        if (out_done[b])
+            cudaEventDestroy(out_done[b]);
+    }
+    if (cin)
+        cudaStreamDestroy(cin);
+    if (cout)
+        cudaStreamDestroy(cout);
+    if (rc == SNLM_OK)
+        rc = r1 != SNLM_OK ? r1 : (r2 != SNLM_OK ? r2 : r3);
     if (rc != SNLM_OK)
         return rc;
     return snlm_device_error(st);

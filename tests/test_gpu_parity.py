@@ -246,6 +246,42 @@ def test_denoise_host_entry_point(dev, api, orc):
     assert np.array_equal(out, out2)
 
 
+def test_pipelined_host_entry_point_equals_single_calls(dev, api, orc):
+    import ctypes
+
+    import torch
+    from paper_1407_2343_gb300 import _lib
+
+    # five images of different content: pinned CPU tensors and pageable arrays mixed;
+    # every result equals the synchronous single-image call bit for bit
+    sigma, S, K = 20.0, 10, 3
+    h = orc.default_h(sigma, K)
+    imgs = [synth.noisy_image(140, 190, sigma, seed=20 + i, dtype="u8") for i in range(5)]
+    hosts = [torch.from_numpy(im).pin_memory() if i % 2 == 0 else im for i, im in enumerate(imgs)]
+    outs = [torch.empty((140, 190), dtype=torch.float32).pin_memory() if i % 2 == 0 else None for i in range(5)]
+    outs = [o if o is not None else np.empty((140, 190), np.float32) for o in outs]
+    got = api.snlm_denoise_host_many(hosts, S, K, h, "box", "SURE", sigma, outs=outs)
+    for i, im in enumerate(imgs):
+        single = api.snlm_denoise_host(im, S, K, h, "box", "SURE", sigma)
+        g = got[i].numpy() if isinstance(got[i], torch.Tensor) else got[i]
+        assert np.array_equal(g, single), i
+    ref, _ = orc.snlm(imgs[3].astype(np.float64), S, K, h, order="SURE", sigma=sigma)
+    assert np.abs(got[3] - ref).max() <= TOL
+    assert api.snlm_denoise_host_many([], S, K, h, "box", "SURE", sigma) == []
+    with pytest.raises(ValueError):
+        api.snlm_denoise_host_many([imgs[0], imgs[1][:, :100]], S, K, h, "box", "SURE", sigma)
+    # C level: a NULL entry or a negative count is an argument error and writes nothing
+    lib = _lib.load()
+    out = np.full((140, 190), 7.0, np.float32)
+    iarr = (ctypes.c_void_p * 2)(imgs[0].ctypes.data, None)
+    oarr = (ctypes.c_void_p * 2)(out.ctypes.data, out.ctypes.data)
+    assert lib.snlm_denoise_host_many(iarr, oarr, 2, api.U8, 140, 190, 190, S, K, h, 0, 3, sigma, 0.0,
+                                      None) == api.ERR_ARG
+    assert lib.snlm_denoise_host_many(iarr, oarr, -1, api.U8, 140, 190, 190, S, K, h, 0, 3, sigma, 0.0,
+                                      None) == api.ERR_ARG
+    assert (out == 7.0).all()
+
+
 def test_argument_errors_leave_output_untouched(dev, api):
     import ctypes
 
