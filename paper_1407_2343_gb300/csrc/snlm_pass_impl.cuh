@@ -858,10 +858,16 @@ __device__ __forceinline__ void unit_epilogue(const PassArgs &p, float *smem, in
         if (p.partials) {
             // deterministic reduction: float warp tree, then the warps in order in fp64
             __shared__ float red[kWarpsPerCta][6];
+            // without the f_rc input only sum [5] is formed; the others are zero
             const int k0 = p.aux_rc.ptr ? 0 : 5;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                float v = k >= k0 ? s[k] : 0.f;
+                if (k < k0) {
+                    if (lane == 0)
+                        red[wid][k] = 0.f;
+                    continue;
+                }
+                float v = s[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
                     v += __shfl_xor_sync(0xffffffffu, v, o);
