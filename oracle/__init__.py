@@ -17,6 +17,9 @@ Functions and the passages they follow:
   nlm_1d         Eq. (4) and, when asked, the divergence of Eq. (24) (Alg. 3)
   snlm           Alg. 4 with Eqs. (14), (19), (25); orders RC, CR, AVG, SURE
   snlm_parts     the intermediate images and derivative maps of Alg. 4
+  bf_params      sigma_s and sigma_r of the bilateral post-filter (Sec. IV-A)
+  bilateral      the bilateral post-filter, Eq. (BF) of Sec. III-B
+  snlm_full      SNLM[f]: Alg. 4 followed by the bilateral post-filter (Sec. III-B)
 """
 from __future__ import annotations
 
@@ -76,6 +79,10 @@ def _load():
         lib.orc_snlm.restype = ci
         lib.orc_snlm_parts.argtypes = [dp, i64, i64, ci, ci, cd, ci, cd, dp, dp, dp, dp, dp, dp, ci]
         lib.orc_snlm_parts.restype = ci
+        lib.orc_bf_params.argtypes = [cd, dp, dp]
+        lib.orc_bf_params.restype = None
+        lib.orc_bilateral.argtypes = [dp, i64, i64, cd, cd, dp, ci]
+        lib.orc_bilateral.restype = ci
         lib.orc_max_threads.argtypes = []
         lib.orc_max_threads.restype = ci
         _lib = lib
@@ -188,6 +195,33 @@ def snlm_parts(img, S: int, K: int, h: float, prof="box", beta: float | None = N
     if rc != 0:
         raise ValueError(f"oracle snlm_parts rejected its arguments (rc={rc})")
     return parts
+
+
+def bf_params(sigma: float):
+    """(sigma_s, sigma_r) of the bilateral post-filter for noise level sigma (Sec. IV-A)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _load().orc_bf_params(float(sigma), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def bilateral(img, sigma_s: float, sigma_r: float, nthreads: int = 0):
+    """Eq. (BF) of Sec. III-B on an (H, W) image (support [-3 sigma_s, 3 sigma_s]^2)."""
+    x = _f64(img)
+    H, W = x.shape
+    out = np.empty_like(x)
+    rc = _load().orc_bilateral(_ptr(x), H, W, float(sigma_s), float(sigma_r), _ptr(out), _nt(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle bilateral rejected its arguments (rc={rc})")
+    return out
+
+
+def snlm_full(img, S: int, K: int, h: float, prof="box", beta: float | None = None, order="SURE",
+              sigma: float = 0.0, sigma_s: float | None = None, sigma_r: float | None = None, nthreads: int = 0):
+    """SNLM[f] of Sec. III-B: Alg. 4, then the bilateral post-filter (its parameters
+    from the rules of Sec. IV-A unless given)."""
+    ss, sr = bf_params(sigma)
+    ft, _ = snlm(img, S, K, h, prof, beta, order=order, sigma=sigma, nthreads=nthreads)
+    return bilateral(ft, ss if sigma_s is None else sigma_s, sr if sigma_r is None else sigma_r, nthreads)
 
 
 def max_threads() -> int:

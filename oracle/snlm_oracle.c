@@ -352,6 +352,51 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
     return 0;
 }
 
+/* Parameters of the bilateral post-filter as functions of the noise level: the
+ * cubic rules learnt in the parameter study (Sec. IV-A). */
+void orc_bf_params(double sigma, double *sigma_s, double *sigma_r)
+{
+    const double s2 = sigma * sigma, s3 = s2 * sigma;
+    *sigma_s = 2.5e-6 * s3 - 3.4e-4 * s2 + 0.021 * sigma + 0.46;
+    *sigma_r = 2.8e-4 * s3 - 0.088 * s2 + 8.0 * sigma - 24.0;
+}
+
+/* Bilateral post-filter of Sec. III-B, Eq. (BF): at pixel i, the average of the
+ * samples f(i - j) over the integer offsets j of Omega = [-3 sigma_s, 3 sigma_s]^2,
+ * weighted by exp(-|j|^2 / (2 sigma_s^2)) * exp(-(f(i - j) - f(i))^2 / (2 sigma_r^2)).
+ * Samples outside the image are read through the symmetric extension (the same
+ * boundary reading as the NLM passes). Direct summation, one pixel at a time. */
+int orc_bilateral(const double *img, int64_t H, int64_t W, double sigma_s, double sigma_r, double *out,
+                  int nthreads)
+{
+    if (H < 1 || W < 1 || !(sigma_s > 0.0) || !(sigma_r > 0.0) || !isfinite(sigma_s))
+        return -1;
+    const int64_t R = (int64_t)floor(3.0 * sigma_s);
+    if (R > 64)
+        return -1;
+    const double two_ss = 2.0 * sigma_s * sigma_s, two_sr = 2.0 * sigma_r * sigma_r;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int64_t y = 0; y < H; ++y) {
+        for (int64_t x = 0; x < W; ++x) {
+            const double c = img[y * W + x];
+            double num = 0.0, den = 0.0;
+            for (int64_t jy = -R; jy <= R; ++jy) {
+                for (int64_t jx = -R; jx <= R; ++jx) {
+                    const double v = img[orc_ext(y - jy, H) * W + orc_ext(x - jx, W)];
+                    const double ws = exp(-(double)(jx * jx + jy * jy) / two_ss);
+                    const double gr = exp(-(v - c) * (v - c) / two_sr);
+                    num += ws * gr * v;
+                    den += ws * gr;
+                }
+            }
+            out[y * W + x] = num / den;
+        }
+    }
+    return 0;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

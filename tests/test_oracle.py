@@ -387,3 +387,85 @@ def test_oracle_rejects_bad_arguments(orc):
         orc.nlm_1d(np.zeros(4), 2, 1, h=0.0)
     with pytest.raises(ValueError):
         orc.snlm(np.zeros((4, 4)), -1, 1, 1.0)
+
+
+# ---- the bilateral post-filter of Sec. III-B (Eq. (BF)) and its parameter rules
+
+def test_bf_parameter_rules_reproduce_the_printed_values(orc):
+    # the cubic rules of Sec. IV-A against the values printed in the captions of the
+    # two bilateral-filtering figures (sigma = 15 and 20) and in Sec. IV-A (sigma = 30),
+    # at the precision the paper prints them
+    pv = paper_values()
+    ss, sr = orc.bf_params(15.0)
+    assert round(ss, 2) == float(pv["bf_sigma_s_at_15"]) and round(sr) == float(pv["bf_sigma_r_at_15"])
+    ss, sr = orc.bf_params(20.0)
+    assert round(ss, 2) == float(pv["bf_sigma_s_at_20"]) and round(sr) == float(pv["bf_sigma_r_at_20"])
+    _, sr = orc.bf_params(30.0)
+    assert abs(sr - float(pv["bf_sigma_r_at_30"])) < 1.0
+
+
+def _spatial_kernel(sigma_s):
+    R = int(np.floor(3.0 * sigma_s))
+    j = np.arange(-R, R + 1)
+    w = np.exp(-(j[:, None] ** 2 + j[None, :] ** 2) / (2.0 * sigma_s ** 2))
+    return w / w.sum()
+
+
+@pytest.mark.parametrize("sigma_s", [0.4, 0.85, 1.0, 1.7])
+def test_bilateral_with_flat_range_kernel_is_the_spatial_gaussian(orc, sigma_s):
+    # sigma_r -> infinity leaves the normalised truncated spatial Gaussian on
+    # [-3 sigma_s, 3 sigma_s]^2; scipy's 'reflect' mode is the half-sample
+    # symmetric extension
+    from scipy import ndimage
+
+    img = np.random.default_rng(3).uniform(0, 255, (23, 31))
+    got = orc.bilateral(img, sigma_s, 1e30)
+    ref = ndimage.correlate(img, _spatial_kernel(sigma_s), mode="reflect")
+    assert np.abs(got - ref).max() < 1e-9
+
+
+def test_bilateral_with_sharp_range_kernel_is_the_identity(orc):
+    img = np.random.default_rng(4).uniform(0, 255, (17, 19))
+    assert np.abs(orc.bilateral(img, 1.2, 1e-30) - img).max() < 1e-12 * 255
+
+
+def test_bilateral_constant_image_unchanged(orc):
+    img = np.full((9, 13), 77.25)
+    assert np.abs(orc.bilateral(img, 1.3, 20.0) - 77.25).max() < 1e-12
+
+
+@pytest.mark.parametrize("x", [3, 4, 5, 6, 7, 8])
+def test_bilateral_two_level_edge_closed_form(orc, x):
+    # a vertical edge (a left of column c0, b from c0 on): the row offsets give the
+    # same factor to both levels and cancel, leaving 1-D sums over the column offsets
+    a, b, c0, sigma_s, sigma_r = 40.0, 140.0, 6, 1.1, 90.0
+    img = np.full((15, 12), a)
+    img[:, c0:] = b
+    R = int(np.floor(3.0 * sigma_s))
+    jx = np.arange(-R, R + 1)
+    ws = np.exp(-jx ** 2 / (2.0 * sigma_s ** 2))
+    same = (x - jx < c0) if x < c0 else (x - jx >= c0)
+    g = np.exp(-(a - b) ** 2 / (2.0 * sigma_r ** 2))
+    own, other = (a, b) if x < c0 else (b, a)
+    expect = (own * ws[same].sum() + g * other * ws[~same].sum()) / (ws[same].sum() + g * ws[~same].sum())
+    got = orc.bilateral(img, sigma_s, sigma_r)
+    assert np.abs(got[4:11, x] - expect).max() < 1e-12
+
+
+def test_bilateral_convex_and_symmetric(orc):
+    rng = np.random.default_rng(5)
+    img = rng.uniform(0, 255, (21, 18))
+    out = orc.bilateral(img, 0.9, 60.0)
+    assert out.min() >= img.min() - 1e-9 and out.max() <= img.max() + 1e-9
+    # symmetric support and extension: transposing or flipping commutes with the filter
+    assert np.abs(orc.bilateral(img.T, 0.9, 60.0) - out.T).max() < 1e-12
+    assert np.abs(orc.bilateral(img[::-1], 0.9, 60.0) - out[::-1]).max() < 1e-12
+    assert np.abs(orc.bilateral(img[:, ::-1], 0.9, 60.0) - out[:, ::-1]).max() < 1e-12
+
+
+def test_snlm_full_is_alg4_then_bilateral(orc):
+    img = np.random.default_rng(6).uniform(0, 255, (24, 20))
+    h = orc.default_h(20.0, 2)
+    ft, _ = orc.snlm(img, 4, 2, h, order="SURE", sigma=20.0)
+    ss, sr = orc.bf_params(20.0)
+    assert np.array_equal(orc.snlm_full(img, 4, 2, h, order="SURE", sigma=20.0), orc.bilateral(ft, ss, sr))
