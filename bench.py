@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rc", action="store_true", help="skip the extra RC-order measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-bf", action="store_true", help="skip the bilateral post-filter measurement")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -227,6 +228,43 @@ def run_reference(a):
                              "sample": f"{side}x{side} top-left crop of the same scene per step"},
             "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure_post_filter(a, api, src, flush, stream, step_ms):
+    """The bilateral post-filter of Sec. III-B on the step's output (parameters from
+    the rules of Sec. IV-A at the scene's sigma): its launch time from the library's
+    trace with L2 flushed between launches, its roofline, and SNLM[f] (Alg. 4 then
+    the filter) in Mpixel/s."""
+    import torch
+
+    ss, sr = api.snlm_bf_params(a.sigma)
+    R = int(math.floor(3.0 * float(np.float32(ss))))
+    dst = torch.empty_like(src)
+    for _ in range(3):
+        api.snlm_bilateral(src, ss, sr, out=dst, stream=stream)
+    torch.cuda.synchronize()
+    n = 50
+    api.snlm_trace_read()
+    api.snlm_trace_enable(True)
+    for _ in range(n):
+        flush.zero_()
+        api.snlm_bilateral(src, ss, sr, out=dst, stream=stream)
+    torch.cuda.synchronize()
+    api.snlm_trace_enable(False)
+    ms = [m for name, m in api.snlm_trace_read(1 << 16) if name == "bilateral"]
+    avg = sum(ms) / len(ms)
+    px = src.numel()
+    taps = (2 * R + 1) ** 2 - 1
+    ops = 5 * taps * px
+    achieved = ops / (avg * 1e-3) / 1e12
+    return {"sigma_s": ss, "sigma_r": sr, "R": R, "launches": len(ms), "avg_launch_ms": avg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+                         "unit": "Tops/s (FP32 lane-ops)", "frac": achieved / ALU_PEAK_TOPS,
+                         "ops_per_tap": 5, "taps_per_pixel": taps,
+                         "sfu": {"achieved_Texp_s": taps * px / (avg * 1e-3) / 1e12, "peak_Texp_s": SFU_PEAK_TEXP,
+                                 "frac": taps * px / (avg * 1e-3) / 1e12 / SFU_PEAK_TEXP},
+                         "dram_bytes_algorithmic": 8 * px},
+            "snlm_full_Mpixel_s": px / ((step_ms + avg) * 1e-3) / 1e6}
 
 
 def measure_batched(a, dev, stream):
@@ -479,6 +517,10 @@ def run_ours(a):
                        "result_equals_device_path": same,
                        "single_call": {"value": job_rate(world, n_e2e * px, t_single) / 1e6, "unit": "Mpixel/s",
                                        "api": "snlm_denoise_host, one synchronous call per step"}}
+
+    if not a.no_bf:
+        step()
+        line["post_filter"] = measure_post_filter(a, api, out, flush, stream, dev_ms_max / a.steps)
 
     if not a.no_batch:
         line["batched"] = measure_batched(a, dev, stream)

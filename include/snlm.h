@@ -133,6 +133,40 @@ int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host
                            float beta, void *stream);
 
 /*
+ * Bilateral post-filter of Sec. III-B, Eq. (BF): out(i) is the average of in(i - j)
+ * over the integer offsets j of [-R, R]^2, R = floor(3 sigma_s), with weights
+ * exp(-|j|^2 / (2 sigma_s^2)) * exp(-(in(i - j) - in(i))^2 / (2 sigma_r^2));
+ * samples outside the image are read through the half-sample symmetric extension.
+ * Computed exactly (direct sum, FP32, one ex2 per tap), not through an
+ * approximation of the range kernel.
+ *   in   DEVICE float32, H rows of in_pitch >= W elements.
+ *   out  DEVICE float32, H rows of out_pitch >= W elements; must not overlap in.
+ *   sigma_s > 0, sigma_r > 0, both finite; R <= 8 (sigma_s < 3), else
+ *   SNLM_ERR_UNSUPPORTED. Asynchronous on `stream`.
+ */
+int snlm_bilateral(const float *in, int H, int W, int in_pitch, float sigma_s, float sigma_r, float *out,
+                   int out_pitch, void *stream);
+
+/*
+ * The post-filter's parameters as functions of the noise level sigma >= 0: the
+ * cubic rules learnt in Sec. IV-A,
+ *   sigma_s = 2.5e-6 sigma^3 - 3.4e-4 sigma^2 + 0.021 sigma + 0.46,
+ *   sigma_r = 2.8e-4 sigma^3 - 0.088 sigma^2 + 8 sigma - 24
+ * (evaluated in double, returned as float). SNLM_ERR_ARG for a negative or
+ * non-finite sigma or a NULL output.
+ */
+int snlm_bf_params(float sigma, float *sigma_s, float *sigma_r);
+
+/*
+ * SNLM[f] of Sec. III-B: snlm_denoise followed by snlm_bilateral. Arguments as in
+ * snlm_denoise, plus the post-filter's sigma_s and sigma_r; when either is <= 0
+ * both come from snlm_bf_params(sigma) (which needs sigma > ~3.2 for sigma_r > 0).
+ * The intermediate image comes from the library's pool. Asynchronous on `stream`.
+ */
+int snlm_denoise_bf(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
+                    int order, float sigma, float beta, float sigma_s, float sigma_r, float *out, void *stream);
+
+/*
  * One 1-D NLM pass (Eq. (4)) over n_lines signals, with the derivative chain of
  * Eq. (24) when delta_out is given (the computation of Alg. 3).
  *   x          DEVICE, samples of type dtype; sample i of line l is at
@@ -266,7 +300,8 @@ typedef enum {
     SNLM_K_SET_THETA = 6,      /* writes the fixed weights of the RC / CR / AVG orders */
     SNLM_K_PATCH_DIST = 7,     /* patch distances of Eq. (3) */
     SNLM_K_LINE_PASS = 8,      /* snlm_nlm_1d pass over arbitrary strided lines */
-    SNLM_K_BATCH = 9           /* one persistent batch kernel (one K class) */
+    SNLM_K_BATCH = 9,          /* one persistent batch kernel (one K class) */
+    SNLM_K_BILATERAL = 10      /* bilateral post-filter of Sec. III-B (Eq. (BF)) */
 } snlm_kernel_kind;
 
 int snlm_trace_enable(int enable);

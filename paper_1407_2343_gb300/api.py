@@ -212,6 +212,49 @@ def snlm_denoise_host_many(imgs, S: int, K: int, h: float | None = None, profile
     return outs
 
 
+def snlm_bf_params(sigma: float):
+    """(sigma_s, sigma_r) of the bilateral post-filter for noise level sigma (Sec. IV-A)."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(_lib.load().snlm_bf_params(float(sigma), ctypes.byref(a), ctypes.byref(b)), "snlm_bf_params")
+    return a.value, b.value
+
+
+def snlm_bilateral(x, sigma_s: float, sigma_r: float, out=None, stream=None):
+    """Bilateral post-filter of Sec. III-B (Eq. (BF)) of a 2-D float32 device tensor
+    with unit column stride; returns out (float32, contiguous unless given)."""
+    torch = _torch()
+    if x.dim() != 2 or x.dtype != torch.float32 or x.stride(1) != 1:
+        raise ValueError("x must be a 2-D float32 tensor with unit column stride")
+    H, W = x.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=x.device)
+    if out.shape != x.shape or out.dtype != torch.float32 or out.stride(1) != 1:
+        raise ValueError("out must be float32 with x's shape and unit column stride")
+    rc = _lib.load().snlm_bilateral(_ptr(x), int(H), int(W), int(x.stride(0)), float(sigma_s), float(sigma_r),
+                                    _ptr(out), int(out.stride(0)), _stream_ptr(stream))
+    _check(rc, "snlm_bilateral")
+    return out
+
+
+def snlm_denoise_bf(img, S: int, K: int, h: float | None = None, profile="box", order="SURE",
+                    sigma: float | None = None, beta: float = 0.0, sigma_s: float = 0.0, sigma_r: float = 0.0,
+                    out=None, stream=None):
+    """SNLM[f] of Sec. III-B: Alg. 4, then the bilateral post-filter (its parameters
+    from the rules of Sec. IV-A when sigma_s or sigma_r is <= 0)."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    h = _h_for(h, sigma, K, profile, beta)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    if out.shape != (H, W) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 (H, W) tensor")
+    rc = _lib.load().snlm_denoise_bf(_ptr(img), dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                     _order(order), float(sigma or 0.0), float(beta or 0.0), float(sigma_s),
+                                     float(sigma_r), _ptr(out), _stream_ptr(stream))
+    _check(rc, "snlm_denoise_bf")
+    return out
+
+
 def snlm_nlm_1d(x, S: int, K: int, h: float, profile="box", beta: float = 0.0, fhat=None,
                 delta_in=None, delta_out=None, stream=None):
     """One 1-D NLM pass (Eq. (4)) over the rows of a 2-D device tensor `x`

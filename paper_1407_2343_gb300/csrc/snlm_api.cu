@@ -109,8 +109,9 @@ Pool &pool()
 }
 
 // Returns scratch of at least `need` bytes on the current device, slot `slot`
-// (0: denoise scratch, 1 and 3: host-call inputs, 2 and 4: host-call outputs).
-constexpr int kPoolSlots = 5;
+// (0: denoise scratch, 1 and 3: host-call inputs, 2 and 4: host-call outputs,
+// 5: the output of Alg. 4 before the bilateral post-filter).
+constexpr int kPoolSlots = 6;
 void *pool_get(size_t need, int slot)
 {
     int dev = 0;
@@ -343,6 +344,33 @@ int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int
         return SNLM_ERR_NOMEM;
     return denoise_core(img, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta, out, ws, nullptr,
                         static_cast<cudaStream_t>(stream));
+}
+
+int snlm_denoise_bf(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
+                    int order, float sigma, float beta, float sigma_s, float sigma_r, float *out, void *stream)
+{
+    if (!(sigma_s > 0.f) || !(sigma_r > 0.f)) {
+        if (snlm_bf_params(sigma, &sigma_s, &sigma_r) != SNLM_OK || !(sigma_r > 0.f) || !(sigma_s > 0.f))
+            return SNLM_ERR_ARG;
+    }
+    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31) || !is_device_ptr(img))
+        return SNLM_ERR_ARG;
+    if (!std::isfinite(sigma_s) || !std::isfinite(sigma_r) || !is_device_ptr(out))
+        return SNLM_ERR_ARG;
+    if (bilateral_radius(sigma_s) > kBfMaxR)
+        return SNLM_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float *mid = static_cast<float *>(pool_get((size_t)H * W * sizeof(float), 5));
+    void *ws = pool_get(ws_layout(H, W, S, order).total, 0);
+    if (!mid || !ws)
+        return SNLM_ERR_NOMEM;
+    rc = denoise_core(img, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta, mid, ws, nullptr, st);
+    if (rc != SNLM_OK)
+        return rc;
+    return run_bilateral(mid, H, W, W, sigma_s, sigma_r, out, W, st);
 }
 
 int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, int S, int K,
@@ -586,7 +614,7 @@ const char *snlm_kernel_name(int kind)
 {
     // low byte: snlm_kernel_kind; bits 8..11: how the patch distances were
     // reduced; bit 12: the pass moved its data with TMA bulk tensor copies
-    static const char *names[10][4] = {
+    static const char *names[11][4] = {
         {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
         {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
         {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
@@ -597,6 +625,7 @@ const char *snlm_kernel_name(int kind)
         {"patch_dist", "patch_dist/slide", "patch_dist/block", "patch_dist/fir"},
         {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir"},
         {"batch", "batch", "batch", "batch"},
+        {"bilateral", "bilateral", "bilateral", "bilateral"},
     };
     static const char *tma_names[4][3] = {
         {"row_pass/slide/tma", "row_pass/block/tma", "row_pass/fir/tma"},
@@ -605,7 +634,7 @@ const char *snlm_kernel_name(int kind)
         {"col_pass_sure/slide/tma", "col_pass_sure/block/tma", "col_pass_sure/fir/tma"},
     };
     const int base = kind & 0xff, dm = (kind >> 8) & 0xf, tma = (kind >> 12) & 1;
-    if (kind < 0 || base > 9 || dm > 2 || (kind >> 13) != 0)
+    if (kind < 0 || base > 10 || dm > 2 || (kind >> 13) != 0)
         return "unknown";
     if (tma)
         return base <= 3 ? tma_names[base][dm] : "unknown";

@@ -9,6 +9,7 @@ namespace snlm {
 
 constexpr int kMaxK = 7;           // largest patch half-width compiled
 constexpr int kMaxS = 128;         // largest search half-width accepted
+constexpr int kBfMaxR = 8;         // largest bilateral half-width floor(3 sigma_s) compiled
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
 constexpr int kWarpsPerCta = 4;    // lines per CTA (one warp per line tile)
 constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
@@ -102,6 +103,14 @@ __host__ __device__ inline int tile_positions(int S)
 inline void finish_pass_args(PassArgs &a) { a.tiles = div_up(a.N, tile_positions(a.S)); }
 
 template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
+
+// Bilateral post-filter (snlm_bilateral.cu): argument checks (an snlm_status) and
+// the launch on validated arguments.
+int bilateral_radius(float sigma_s);
+int check_bilateral(const float *in, int H, int W, long long in_pitch, float sigma_s, float sigma_r,
+                    const float *out, long long out_pitch);
+int run_bilateral(const float *in, int H, int W, long long in_pitch, float sigma_s, float sigma_r, float *out,
+                  long long out_pitch, cudaStream_t st);
 // ---- Tensor-memory-accelerator (TMA) movement of a pass (sm_90+ bulk tensor copies).
 // Each array a pass reads (the line windows and the tile inputs of the epilogue)
 // gets a 2-D tensor map over (dim0, dim1) = (positions, lines) for row-like views
