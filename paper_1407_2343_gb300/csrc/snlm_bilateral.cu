@@ -14,7 +14,8 @@
 //
 // A CTA filters a 128 x 16 tile: it stages the tile with its R-wide halo in shared
 // memory (reflected at the image borders), then each thread filters 4 consecutive
-// pixels of 2 rows, reading each window row with 16-byte shared-memory loads.
+// pixels of 2 rows, reading each window row with 16-byte shared-memory loads and
+// treating its pixels in pairs with packed FP32x2 arithmetic (the ex2 stays scalar).
 #include "snlm_host.h"
 #include "snlm_internal.h"
 
@@ -34,9 +35,57 @@ struct BfArgs {
     float *out;
     long long in_pitch, out_pitch;
     int H, W;
-    float cr;                // -log2(e) / (2 sigma_r^2)
-    float lw[kBfTaps];       // lw[(dy) * (2R + 1) + dx] = -log2(e) ((dx-R)^2 + (dy-R)^2) / (2 sigma_s^2)
+    float2 cr2;              // (cr, cr), cr = -log2(e) / (2 sigma_r^2)
+    float2 lw2[kBfTaps];     // (lw, lw) of tap dy * (2R + 1) + dx: -log2(e) ((dx-R)^2 + (dy-R)^2) / (2 sigma_s^2)
 };
+
+// Two floats in one 64-bit register pair for the packed FP32x2 instructions (two
+// pixels per issue slot).
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f32x2 pk2(float2 v) { return pk(v.x, v.y); }
+__device__ __forceinline__ float lo_of(f32x2 v)
+{
+    float a;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(a) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi_of(f32x2 v)
+{
+    float a;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(a) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // Half-sample symmetric extension into [0, n), 2n-periodic.
 __device__ __forceinline__ int bf_reflect(int x, int n)
@@ -82,13 +131,15 @@ __global__ void __launch_bounds__(kBfWarps * 32) bilateral_kernel(const __grid_c
         const int y = y0 + ty;
         if (y >= p.H)
             break;
-        float c[kBfPx], num[kBfPx], den[kBfPx];
+        // pixel pairs (0, 1) and (2, 3): centre, numerator and denominator as float pairs
+        f32x2 C2[kBfPx / 2], N2[kBfPx / 2], D2[kBfPx / 2];
 #pragma unroll
-        for (int k = 0; k < kBfPx; ++k) {
-            c[k] = tile[(ty + R) * SW + 4 * lane + R + k];
-            num[k] = 0.f;
-            den[k] = 1.f;                                 // the centre tap
+        for (int q = 0; q < kBfPx / 2; ++q) {
+            C2[q] = pk(tile[(ty + R) * SW + 4 * lane + R + 2 * q], tile[(ty + R) * SW + 4 * lane + R + 2 * q + 1]);
+            N2[q] = pk(0.f, 0.f);
+            D2[q] = pk(1.f, 1.f);                         // the centre tap
         }
+        const f32x2 cr2 = pk2(p.cr2);
 #pragma unroll
         for (int dy = 0; dy < D; ++dy) {
             float v[4 * NV];
@@ -101,18 +152,35 @@ __global__ void __launch_bounds__(kBfWarps * 32) bilateral_kernel(const __grid_c
                 v[4 * b + 2] = t.z;
                 v[4 * b + 3] = t.w;
             }
+            // window pairs starting at every position j (even j: the loaded pairs)
+            f32x2 V2[4 * NV - 1];
 #pragma unroll
-            for (int k = 0; k < kBfPx; ++k) {
+            for (int j = 0; j + 1 < 4 * NV; ++j)
+                V2[j] = pk(v[j], v[j + 1]);
 #pragma unroll
-                for (int dx = 0; dx < D; ++dx) {
+            for (int dx = 0; dx < D; ++dx) {
+                const f32x2 lw = pk2(p.lw2[dy * D + dx]);
+#pragma unroll
+                for (int q = 0; q < kBfPx / 2; ++q) {
                     if (dy == R && dx == R)
                         continue;
-                    const float t = v[k + dx] - c[k];
-                    const float wg = bf_ex2(fmaf(t * p.cr, t, p.lw[dy * D + dx]));
-                    num[k] = fmaf(wg, t, num[k]);
-                    den[k] += wg;
+                    const f32x2 t = sub2(V2[2 * q + dx], C2[q]);
+                    const f32x2 e = fma2(mul2(t, cr2), t, lw);
+                    const f32x2 wg = pk(bf_ex2(lo_of(e)), bf_ex2(hi_of(e)));
+                    N2[q] = fma2(wg, t, N2[q]);
+                    D2[q] = add2(D2[q], wg);
                 }
             }
+        }
+        float c[kBfPx], num[kBfPx], den[kBfPx];
+#pragma unroll
+        for (int q = 0; q < kBfPx / 2; ++q) {
+            c[2 * q] = lo_of(C2[q]);
+            c[2 * q + 1] = hi_of(C2[q]);
+            num[2 * q] = lo_of(N2[q]);
+            num[2 * q + 1] = hi_of(N2[q]);
+            den[2 * q] = lo_of(D2[q]);
+            den[2 * q + 1] = hi_of(D2[q]);
         }
         float o[kBfPx];
 #pragma unroll
@@ -162,14 +230,16 @@ int run_bilateral(const float *in, int H, int W, long long in_pitch, float sigma
     a.W = W;
     const double log2e = 1.4426950408889634;
     const double ss = (double)sigma_s, sr = (double)sigma_r;
-    a.cr = (float)(-log2e / (2.0 * sr * sr));
+    const float cr = (float)(-log2e / (2.0 * sr * sr));
+    a.cr2 = make_float2(cr, cr);
     for (int i = 0; i < kBfTaps; ++i)
-        a.lw[i] = 0.f;
+        a.lw2[i] = make_float2(0.f, 0.f);
     const int D = 2 * R + 1;
     for (int dy = 0; dy < D; ++dy)
         for (int dx = 0; dx < D; ++dx) {
             const double j2 = (double)((dx - R) * (dx - R) + (dy - R) * (dy - R));
-            a.lw[dy * D + dx] = (float)(-log2e * j2 / (2.0 * ss * ss));
+            const float lw = (float)(-log2e * j2 / (2.0 * ss * ss));
+            a.lw2[dy * D + dx] = make_float2(lw, lw);
         }
     TraceScope ts(SNLM_K_BILATERAL, st);
     cudaError_t e;
