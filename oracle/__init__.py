@@ -17,6 +17,7 @@ Functions and the passages they follow:
   nlm_1d         Eq. (4) and, when asked, the divergence of Eq. (24) (Alg. 3)
   snlm           Alg. 4 with Eqs. (14), (19), (25); orders RC, CR, AVG, SURE
   snlm_parts     the intermediate images and derivative maps of Alg. 4
+  nlm_2d         the 2-D non-local means of Eqs. (1)-(2) (the comparison workload)
   bf_params      sigma_s and sigma_r of the bilateral post-filter (Sec. IV-A)
   bilateral      the bilateral post-filter, Eq. (BF) of Sec. III-B
   snlm_full      SNLM[f]: Alg. 4 followed by the bilateral post-filter (Sec. III-B)
@@ -79,6 +80,8 @@ def _load():
         lib.orc_snlm.restype = ci
         lib.orc_snlm_parts.argtypes = [dp, i64, i64, ci, ci, cd, ci, cd, dp, dp, dp, dp, dp, dp, ci]
         lib.orc_snlm_parts.restype = ci
+        lib.orc_nlm_2d.argtypes = [dp, i64, i64, ci, ci, ci, ci, cd, ci, cd, dp, ci]
+        lib.orc_nlm_2d.restype = ci
         lib.orc_bf_params.argtypes = [cd, dp, dp]
         lib.orc_bf_params.restype = None
         lib.orc_bilateral.argtypes = [dp, i64, i64, cd, cd, dp, ci]
@@ -195,6 +198,28 @@ def snlm_parts(img, S: int, K: int, h: float, prof="box", beta: float | None = N
     if rc != 0:
         raise ValueError(f"oracle snlm_parts rejected its arguments (rc={rc})")
     return parts
+
+
+def nlm_2d(img, S, K, h: float, prof="box", alpha: float | None = None, nthreads: int = 0):
+    """Eqs. (1)-(2) on an (H, W) image. S and K are ints (square window and patch) or
+    (Sy, Sx) / (Ky, Kx) pairs; alpha defaults to K/2 (the larger K)."""
+    x = _f64(img)
+    H, W = x.shape
+    Sy, Sx = (S, S) if np.isscalar(S) else S
+    Ky, Kx = (K, K) if np.isscalar(K) else K
+    out = np.empty_like(x)
+    a = float(alpha if alpha is not None else default_beta(max(Ky, Kx)))
+    rc = _load().orc_nlm_2d(_ptr(x), H, W, int(Sy), int(Sx), int(Ky), int(Kx), float(h), _profile_id(prof), a,
+                            _ptr(out), _nt(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle nlm_2d rejected its arguments (rc={rc})")
+    return out
+
+
+def default_h_2d(sigma: float, K: int, prof="box", alpha: float | None = None) -> float:
+    """h = sigma * sqrt(sum_k G(k)) over the (2K+1)^2 patch (the 2-D form of the 1-D rule)."""
+    g = profile(K, prof, alpha)
+    return float(sigma * np.sqrt(g.sum() ** 2))
 
 
 def bf_params(sigma: float):

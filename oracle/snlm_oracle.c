@@ -352,6 +352,50 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
     return 0;
 }
 
+/* Non-local means of Eqs. (1)-(2) (Sec. I), the comparison workload of the run-time
+ * tables of Sec. IV-B: at pixel i, the average of f(j) over the (2Sy+1) x (2Sx+1)
+ * window centred at i, weighted by exp(-(1/h^2) sum_{k in P} G(k) (f(i+k) - f(j+k))^2)
+ * with P = [-Ky, Ky] x [-Kx, Kx] and G(k1, k2) = g(k1) g(k2) (box: 1; Gaussian:
+ * exp(-(k1^2 + k2^2) / (2 alpha^2)), the product of the 1-D profiles). Samples are
+ * read through the symmetric extension (the boundary reading of the 1-D passes,
+ * applied along each axis). Direct evaluation, O(S^2 K^2) per pixel. */
+int orc_nlm_2d(const double *img, int64_t H, int64_t W, int Sy, int Sx, int Ky, int Kx, double h, int profile,
+               double alpha, double *out, int nthreads)
+{
+    if (H < 1 || W < 1 || Sy < 0 || Sx < 0 || Ky < 0 || Kx < 0 || Ky > 64 || Kx > 64 || !(h > 0.0))
+        return -1;
+    double gy[2 * 64 + 1], gx[2 * 64 + 1];
+    orc_profile(Ky, profile, alpha, gy);
+    orc_profile(Kx, profile, alpha, gx);
+    const double ih2 = 1.0 / (h * h);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+#endif
+    for (int64_t y = 0; y < H; ++y) {
+        for (int64_t x = 0; x < W; ++x) {
+            double num = 0.0, den = 0.0;
+            for (int64_t sy = -Sy; sy <= Sy; ++sy) {
+                for (int64_t sx = -Sx; sx <= Sx; ++sx) {
+                    double d = 0.0;
+                    for (int64_t k1 = -Ky; k1 <= Ky; ++k1) {
+                        const int64_t ri = orc_ext(y + k1, H), rj = orc_ext(y + sy + k1, H);
+                        for (int64_t k2 = -Kx; k2 <= Kx; ++k2) {
+                            const double a = img[ri * W + orc_ext(x + k2, W)];
+                            const double b = img[rj * W + orc_ext(x + sx + k2, W)];
+                            d += gy[k1 + Ky] * gx[k2 + Kx] * (a - b) * (a - b);
+                        }
+                    }
+                    const double w = exp(-d * ih2);
+                    num += w * img[orc_ext(y + sy, H) * W + orc_ext(x + sx, W)];
+                    den += w;
+                }
+            }
+            out[y * W + x] = num / den;
+        }
+    }
+    return 0;
+}
+
 /* Parameters of the bilateral post-filter as functions of the noise level: the
  * cubic rules learnt in the parameter study (Sec. IV-A). */
 void orc_bf_params(double sigma, double *sigma_s, double *sigma_r)

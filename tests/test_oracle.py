@@ -469,3 +469,60 @@ def test_snlm_full_is_alg4_then_bilateral(orc):
     ft, _ = orc.snlm(img, 4, 2, h, order="SURE", sigma=20.0)
     ss, sr = orc.bf_params(20.0)
     assert np.array_equal(orc.snlm_full(img, 4, 2, h, order="SURE", sigma=20.0), orc.bilateral(ft, ss, sr))
+
+
+# ---- the 2-D non-local means of Eqs. (1)-(2) (the comparison workload of Sec. IV-B)
+
+@pytest.mark.parametrize("prof", ["box", "gauss"])
+def test_nlm_2d_with_line_window_and_patch_is_the_1d_pass(orc, prof):
+    # a 1 x (2S+1) window and a 1 x (2K+1) patch reduce Eqs. (1)-(2) to the row pass
+    # of Eq. (4); the transposed shapes to the column pass
+    img = synth.noisy_image(11, 14, 20.0, seed=8, dtype="u8").astype(np.float64)
+    S, K, h = 3, 2, 35.0
+    beta = 1.0
+    fr = orc.snlm_parts(img, S, K, h, prof, beta)["fr"]
+    fc = orc.snlm_parts(img, S, K, h, prof, beta)["fc"]
+    np.testing.assert_allclose(orc.nlm_2d(img, (0, S), (0, K), h, prof, beta), fr, rtol=1e-13, atol=1e-11)
+    np.testing.assert_allclose(orc.nlm_2d(img, (S, 0), (K, 0), h, prof, beta), fc, rtol=1e-13, atol=1e-11)
+
+
+@pytest.mark.parametrize("S", [1, 3])
+def test_nlm_2d_flat_weights_give_the_window_mean(orc, S):
+    # h -> infinity: the mean of the (2S+1)^2 window, read through the symmetric
+    # extension (scipy's 'reflect' mode)
+    from scipy import ndimage
+
+    img = np.random.default_rng(9).uniform(0, 255, (13, 17))
+    got = orc.nlm_2d(img, S, 2, 1e30)
+    ref = ndimage.uniform_filter(img, size=2 * S + 1, mode="reflect")
+    assert np.abs(got - ref).max() < 1e-9
+
+
+def test_nlm_2d_identity_constant_and_symmetry(orc):
+    rng = np.random.default_rng(10)
+    img = rng.uniform(0, 255, (12, 15))
+    np.testing.assert_allclose(orc.nlm_2d(img, 2, 1, 1e-30), img, rtol=0, atol=1e-12)
+    assert np.abs(orc.nlm_2d(np.full((9, 8), 33.5), 2, 2, 10.0) - 33.5).max() < 1e-12
+    out = orc.nlm_2d(img, 2, 1, 60.0, "gauss", 1.0)
+    np.testing.assert_allclose(orc.nlm_2d(img.T.copy(), 2, 1, 60.0, "gauss", 1.0), out.T, rtol=1e-13, atol=1e-11)
+    assert out.min() >= img.min() - 1e-9 and out.max() <= img.max() + 1e-9
+
+
+def test_nlm_2d_gaussian_patch_kernel_is_the_2d_gaussian(orc):
+    # Eq. (2) written with the 2-D Gaussian exp(-|k|^2 / (2 alpha^2)) at one interior
+    # pixel, against the oracle's product of 1-D profiles
+    img = synth.noisy_image(12, 12, 20.0, seed=12, dtype="f32").astype(np.float64)
+    S, K, h, alpha = 2, 2, 40.0, 1.3
+    y, x = 6, 5
+    num = den = 0.0
+    for sy in range(-S, S + 1):
+        for sx in range(-S, S + 1):
+            d = 0.0
+            for k1 in range(-K, K + 1):
+                for k2 in range(-K, K + 1):
+                    G = math.exp(-(k1 * k1 + k2 * k2) / (2 * alpha ** 2))
+                    d += G * (img[y + k1, x + k2] - img[y + sy + k1, x + sx + k2]) ** 2
+            w = math.exp(-d / h ** 2)
+            num += w * img[y + sy, x + sx]
+            den += w
+    assert abs(orc.nlm_2d(img, S, K, h, "gauss", alpha)[y, x] - num / den) < 1e-10
