@@ -99,6 +99,7 @@ def parse():
     ap.add_argument("--no-rc", action="store_true", help="skip the extra RC-order measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-bf", action="store_true", help="skip the bilateral post-filter measurement")
+    ap.add_argument("--no-nlm2d", action="store_true", help="skip the 2-D NLM comparison")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -265,6 +266,63 @@ def measure_post_filter(a, api, src, flush, stream, step_ms):
                                  "frac": taps * px / (avg * 1e-3) / 1e12 / SFU_PEAK_TEXP},
                          "dram_bytes_algorithmic": 8 * px},
             "snlm_full_Mpixel_s": px / ((step_ms + avg) * 1e-3) / 1e6}
+
+
+def measure_nlm2d(a, api, dev, stream, flush):
+    """The comparison of the run-time tables of Sec. IV-B on this GPU: the 2-D NLM of
+    Eqs. (1)-(2) (S = 20, K = 5, box and Gaussian, evaluated exactly) against Alg. 4
+    and SNLM[f] on the same synthetic scenes (N = 256, 512, 1024 and the benchmark's
+    size), device times from the library's trace (L2 flushed between launches), and
+    the PSNR of each output against the clean scene."""
+    import torch
+    from paper_1407_2343_gb300 import synth
+
+    S, K, sigma = 20, 5, a.sigma
+    rows = []
+    for n in sorted({256, 512, 1024, a.size}):
+        sc = synth.scene(n, n, sigma, seed=7)
+        img = torch.from_numpy(synth.store(sc.noisy, a.dtype)).to(dev)
+        out = torch.empty((n, n), dtype=torch.float32, device=dev)
+        ws = torch.empty(api.snlm_workspace_bytes(n, n, "SURE"), dtype=torch.uint8, device=dev)
+        row = {"N": n}
+        for prof in ("box", "gauss"):
+            h1 = api.snlm_default_h(sigma, K, prof)
+            g = np.exp(-np.arange(-K, K + 1) ** 2 / (2.0 * (K / 2.0) ** 2)) if prof == "gauss" else np.ones(2 * K + 1)
+            h2 = sigma * float(g.sum())
+
+            def timed(fn, reps):
+                fn()
+                torch.cuda.synchronize()
+                api.snlm_trace_read()
+                api.snlm_trace_enable(True)
+                for _ in range(reps):
+                    flush.zero_()
+                    fn()
+                torch.cuda.synchronize()
+                api.snlm_trace_enable(False)
+                return sum(ms for _, ms in api.snlm_trace_read(1 << 16)) / reps
+
+            reps2 = 2 if n >= 2048 else 5
+            t_nlm = timed(lambda: api.snlm_nlm_2d(img, S, K, h2, prof, out=out, stream=stream), reps2)
+            psnr_nlm = psnr(out.cpu().numpy(), sc.clean)
+            t_snlm = timed(lambda: api.snlm_denoise_ws(img, S, K, h1, prof, "SURE", sigma, out=out, workspace=ws,
+                                                       stream=stream), 10)
+            psnr_snlm = psnr(out.cpu().numpy(), sc.clean)
+            t_full = timed(lambda: api.snlm_denoise_bf(img, S, K, h1, prof, "SURE", sigma, out=out, stream=stream), 10)
+            psnr_full = psnr(out.cpu().numpy(), sc.clean)
+            row[prof] = {"nlm_2d_ms": t_nlm, "snlm_alg4_ms": t_snlm, "snlm_full_ms": t_full,
+                         "speedup_alg4": t_nlm / t_snlm, "speedup_full": t_nlm / t_full,
+                         "psnr_noisy": psnr(sc.noisy, sc.clean), "psnr_nlm_2d": psnr_nlm,
+                         "psnr_snlm_alg4": psnr_snlm, "psnr_snlm_full": psnr_full}
+        rows.append(row)
+    return {"S": S, "K": K, "sigma": sigma, "dtype": a.dtype, "rows": rows,
+            "note": "2-D NLM evaluated exactly on the GPU (every window offset, separable patch sum); "
+                    "h = sigma * sqrt(sum of the patch kernel) for both methods"}
+
+
+def psnr(x, clean):
+    mse = float(np.mean((np.asarray(x, np.float64) - clean) ** 2))
+    return 10.0 * math.log10(255.0 ** 2 / mse)
 
 
 def measure_batched(a, dev, stream):
@@ -521,6 +579,9 @@ def run_ours(a):
     if not a.no_bf:
         step()
         line["post_filter"] = measure_post_filter(a, api, out, flush, stream, dev_ms_max / a.steps)
+
+    if not a.no_nlm2d and rank == 0:
+        line["nlm_2d_comparison"] = measure_nlm2d(a, api, dev, stream, flush)
 
     if not a.no_batch:
         line["batched"] = measure_batched(a, dev, stream)

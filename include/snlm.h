@@ -167,6 +167,20 @@ int snlm_denoise_bf(const void *img, int dtype, int H, int W, int pitch, int S, 
                     int order, float sigma, float beta, float sigma_s, float sigma_r, float *out, void *stream);
 
 /*
+ * The 2-D non-local means of Eqs. (1)-(2) (Sec. I), the workload the run-time
+ * tables of Sec. IV-B compare separable NLM against: at pixel i the average of
+ * f(j) over the (2S+1)^2 window centred at i with weights
+ * exp(-(1/h^2) sum_{k in [-K,K]^2} G(k) (f(i+k) - f(j+k))^2), G(k1,k2) = g(k1) g(k2)
+ * (box: 1; Gaussian: exp(-|k|^2 / (2 alpha^2)), alpha <= 0 selects K/2); samples
+ * through the half-sample symmetric extension along each axis. Evaluated exactly
+ * (every offset of the window, the patch sum as two 1-D filters), FP32.
+ *   img  DEVICE, H rows of `pitch` elements of `dtype`; out DEVICE float32 H x W.
+ *   S <= 32 and K <= 7 (else SNLM_ERR_UNSUPPORTED). Asynchronous on `stream`.
+ */
+int snlm_nlm_2d(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
+                float alpha, float *out, void *stream);
+
+/*
  * One 1-D NLM pass (Eq. (4)) over n_lines signals, with the derivative chain of
  * Eq. (24) when delta_out is given (the computation of Alg. 3).
  *   x          DEVICE, samples of type dtype; sample i of line l is at
@@ -301,7 +315,8 @@ typedef enum {
     SNLM_K_PATCH_DIST = 7,     /* patch distances of Eq. (3) */
     SNLM_K_LINE_PASS = 8,      /* snlm_nlm_1d pass over arbitrary strided lines */
     SNLM_K_BATCH = 9,          /* one persistent batch kernel (one K class) */
-    SNLM_K_BILATERAL = 10      /* bilateral post-filter of Sec. III-B (Eq. (BF)) */
+    SNLM_K_BILATERAL = 10,     /* bilateral post-filter of Sec. III-B (Eq. (BF)) */
+    SNLM_K_NLM_2D = 11         /* the 2-D NLM of Eqs. (1)-(2) (comparison workload) */
 } snlm_kernel_kind;
 
 int snlm_trace_enable(int enable);

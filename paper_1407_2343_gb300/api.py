@@ -255,6 +255,21 @@ def snlm_denoise_bf(img, S: int, K: int, h: float | None = None, profile="box", 
     return out
 
 
+def snlm_nlm_2d(img, S: int, K: int, h: float, profile="box", alpha: float = 0.0, out=None, stream=None):
+    """The 2-D non-local means of Eqs. (1)-(2) of a 2-D device tensor (uint8,
+    float16 or float32, unit column stride); returns out (float32, contiguous)."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    if out.shape != (H, W) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 (H, W) tensor")
+    rc = _lib.load().snlm_nlm_2d(_ptr(img), dt, H, W, pitch, int(S), int(K), float(h), _profile(profile),
+                                 float(alpha or 0.0), _ptr(out), _stream_ptr(stream))
+    _check(rc, "snlm_nlm_2d")
+    return out
+
+
 def snlm_nlm_1d(x, S: int, K: int, h: float, profile="box", beta: float = 0.0, fhat=None,
                 delta_in=None, delta_out=None, stream=None):
     """One 1-D NLM pass (Eq. (4)) over the rows of a 2-D device tensor `x`

@@ -614,7 +614,7 @@ const char *snlm_kernel_name(int kind)
 {
     // low byte: snlm_kernel_kind; bits 8..11: how the patch distances were
     // reduced; bit 12: the pass moved its data with TMA bulk tensor copies
-    static const char *names[11][4] = {
+    static const char *names[12][4] = {
         {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
         {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
         {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
@@ -626,6 +626,7 @@ const char *snlm_kernel_name(int kind)
         {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir"},
         {"batch", "batch", "batch", "batch"},
         {"bilateral", "bilateral", "bilateral", "bilateral"},
+        {"nlm_2d", "nlm_2d", "nlm_2d", "nlm_2d"},
     };
     static const char *tma_names[4][3] = {
         {"row_pass/slide/tma", "row_pass/block/tma", "row_pass/fir/tma"},
@@ -634,7 +635,7 @@ const char *snlm_kernel_name(int kind)
         {"col_pass_sure/slide/tma", "col_pass_sure/block/tma", "col_pass_sure/fir/tma"},
     };
     const int base = kind & 0xff, dm = (kind >> 8) & 0xf, tma = (kind >> 12) & 1;
-    if (kind < 0 || base > 10 || dm > 2 || (kind >> 13) != 0)
+    if (kind < 0 || base > 11 || dm > 2 || (kind >> 13) != 0)
         return "unknown";
     if (tma)
         return base <= 3 ? tma_names[base][dm] : "unknown";

@@ -10,6 +10,7 @@ namespace snlm {
 constexpr int kMaxK = 7;           // largest patch half-width compiled
 constexpr int kMaxS = 128;         // largest search half-width accepted
 constexpr int kBfMaxR = 8;         // largest bilateral half-width floor(3 sigma_s) compiled
+constexpr int kMaxS2d = 32;        // largest search half-width of the 2-D NLM
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
 constexpr int kWarpsPerCta = 4;    // lines per CTA (one warp per line tile)
 constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
