@@ -47,9 +47,9 @@ OPS_PER_PAIR = {"plain": 9, "sure": 11}
 # `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
 # --no-cpu-baseline --no-rc` (the first timed step's four passes); valid only while
 # the kernel sources hash to `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "92c72d01d9ff3c96",
-           "bytes_per_launch": {"row_pass_sure/slide": 90.581248e6, "col_pass_sure/block": 179.153408e6,
-                                "col_pass_sure/slide": 96.090624e6, "row_pass_sure/block": 268.020224e6}}
+TRAFFIC = {"sources_sha": "aef327d29fcf1283",
+           "bytes_per_launch": {"row_pass_sure/slide": 90.6816e6, "col_pass_sure/block": 178.894592e6,
+                                "col_pass_sure/slide": 96.681472e6, "row_pass_sure/block": 267.57376e6}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
