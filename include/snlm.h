@@ -338,7 +338,10 @@ const char *snlm_kernel_name(int kind);
  * consecutive smaller requests at the front of the queue (at most max_batch) run
  * as one batch plan (the persistent launch of snlm_batch_plan_*). Each launch
  * copies its inputs in, runs, and copies its results out on its own stream, so
- * launches overlap on the device. SNLM_SERVE_PLAIN serves one request at a time
+ * launches overlap on the device; half of the streams (at least one) have the
+ * device's highest priority and carry the launches of requests below solo_pixels,
+ * so that their blocks are dispatched ahead of those of a large request's pass
+ * already in flight. SNLM_SERVE_PLAIN serves one request at a time
  * through the per-image path and waits for each (the per-request baseline).
  * Results are those of snlm_denoise (bitwise for RC/CR/AVG; SURE within the float
  * rounding of its sums).

@@ -130,6 +130,7 @@ struct snlm_server {
     Slab slab;
     std::vector<cudaStream_t> streams;
     std::vector<char> busy;
+    std::vector<char> high;       // stream created with the device's highest priority
     std::vector<Req> reqs;
     std::vector<int> order;       // submitted ids by arrival time
     size_t next = 0;              // next entry of `order` not yet arrived
@@ -332,12 +333,19 @@ int launch_batch(snlm_server *s, const std::vector<int> &ids, int si, Launch &L,
     return SNLM_OK;
 }
 
-int free_stream(const snlm_server *s)
+// A free stream, of the high-priority half for small launches and of the
+// low-priority half for large ones when one is free, else any free stream.
+int free_stream(const snlm_server *s, bool small)
 {
+    int any = -1;
     for (size_t i = 0; i < s->busy.size(); ++i)
-        if (!s->busy[i])
-            return (int)i;
-    return -1;
+        if (!s->busy[i]) {
+            if ((s->high[i] != 0) == small)
+                return (int)i;
+            if (any < 0)
+                any = (int)i;
+        }
+    return any;
 }
 
 long long pixels(const snlm_serve_request &r) { return (long long)r.H * r.W; }
@@ -348,13 +356,13 @@ bool start_launches(snlm_server *s, int *err)
     bool any = false;
     const bool plain = s->cfg.mode == SNLM_SERVE_PLAIN;
     while (!s->queue.empty()) {
-        const int si = free_stream(s);
+        const int front = s->queue.front();
+        const snlm_serve_request &fr = s->reqs[front].r;
+        const int si = free_stream(s, pixels(fr) < s->cfg.solo_pixels);
         if (si < 0 || (plain && !s->inflight.empty()))
             break;
         Launch L;
         L.stream = si;
-        const int front = s->queue.front();
-        const snlm_serve_request &fr = s->reqs[front].r;
         int launched = 0;
         const bool solo = plain || fr.K < 1 || pixels(fr) >= s->cfg.solo_pixels ||
                           (s->queue.size() == 1 && s->inflight.empty());
@@ -482,11 +490,24 @@ int snlm_server_create(const snlm_server_config *cfg, snlm_server **out)
     s->st.budget_bytes = (long long)s->slab.size;
     s->streams.resize((size_t)c.streams);
     s->busy.assign((size_t)c.streams, 0);
-    for (auto &st : s->streams)
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    s->high.assign((size_t)c.streams, 0);
+    // batched mode: the first half of the streams (at least one) get the device's
+    // highest priority and carry the small launches, so that the block scheduler
+    // dispatches their CTAs ahead of the pending CTAs of a large request's pass
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    const int n_high = c.mode == SNLM_SERVE_PLAIN ? 0 : std::max(1, c.streams / 2);
+    for (size_t i = 0; i < s->streams.size(); ++i) {
+        s->high[i] = (int)i < n_high;
+        if (cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, s->high[i] ? greatest : least) !=
+            cudaSuccess) {
             cudaGetLastError();
-            st = nullptr;
+            s->streams[i] = nullptr;
         }
+    }
     *out = s;
     return SNLM_OK;
 }
