@@ -45,9 +45,10 @@ OPS_PER_PAIR = {"plain": 9, "sure": 11}
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # pass kernels of the 4096^2 u8 SURE step, from one ncu --set full capture of
 # `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
-# --no-cpu-baseline --no-rc` (the first timed step's four passes); valid only while
-# the kernel sources hash to `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "aef327d29fcf1283",
+# --no-cpu-baseline --no-rc --no-bf --no-nlm2d` (the first timed step's four
+# passes); valid only while the pass kernels' sources (PASS_KERNEL_SOURCES) hash to
+# `sources_sha` (profiles/ has the capture's summary).
+TRAFFIC = {"sources_sha": "66422eaeef7ec8c9",
            "bytes_per_launch": {"row_pass_sure/slide": 90.6816e6, "col_pass_sure/block": 178.894592e6,
                                 "col_pass_sure/slide": 96.681472e6, "row_pass_sure/block": 267.57376e6}}
 
@@ -71,13 +72,18 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+# The files the pass kernels are compiled from (their template code, the argument
+# and layout structs, and the K = 5 translation unit); the public header supplies
+# only status constants to them.
+PASS_KERNEL_SOURCES = ("snlm_pass_impl.cuh", "snlm_internal.h", "snlm_pass_k5.cu")
+
+
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_2343_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in PASS_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
