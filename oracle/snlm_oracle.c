@@ -11,7 +11,7 @@
  * precision, with explicit (2K+1)-tap patch sums: no lifting, no running sums,
  * no symmetry reuse. Each function names the passage it follows.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Boundary: half-sample symmetric extension, applied to patch samples and
  *    to search positions alike, repeated with period 2N when the reach S+K
  *    exceeds the signal (the paper comments the extension sentence out in
