@@ -48,9 +48,9 @@ OPS_PER_PAIR = {"plain": 9, "sure": 11}
 # --no-cpu-baseline --no-rc --no-bf --no-nlm2d` (the first timed step's four
 # passes); valid only while the pass kernels' sources (PASS_KERNEL_SOURCES) hash to
 # `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "66422eaeef7ec8c9",
-           "bytes_per_launch": {"row_pass_sure/slide": 90.6816e6, "col_pass_sure/block": 178.894592e6,
-                                "col_pass_sure/slide": 96.681472e6, "row_pass_sure/block": 267.57376e6}}
+TRAFFIC = {"sources_sha": "7d819b9d93eeafd0",
+           "bytes_per_launch": {"row_pass_sure/slide": 90.717696e6, "col_pass_sure/block": 178.725888e6,
+                                "col_pass_sure/slide": 96.91264e6, "row_pass_sure/block": 267.996672e6}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -109,6 +109,9 @@ def parse():
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the benchmark line, time Alg. 4 over S (K = 3) and K (S = 20), "
+                         "box and Gaussian, and print one JSON line")
     return ap.parse_args()
 
 
@@ -606,10 +609,53 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(a):
+    """Run time of Alg. 4 (the SURE order, all four passes) against the search and
+    patch half-widths, the scaling study of the run-time figure of Sec. IV-B: S in
+    {10, 15, 20, 25, 30} at K = 3 and K in {2, ..., 7} at S = 20, box and Gaussian,
+    on the benchmark's scene; device time per step from CUDA events (L2 flushed
+    between steps), median of the steps."""
+    import torch
+    from paper_1407_2343_gb300 import _lib, api, synth
+
+    _lib.load(build_if_missing=True)
+    dev = torch.device("cuda", 0)
+    n = a.size
+    img = torch.from_numpy(synth.noisy_image(n, n, a.sigma, seed=0, dtype=a.dtype)).to(dev)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    ws = torch.empty(api.snlm_workspace_bytes(n, n, a.order), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    points = [(S, 3) for S in (10, 15, 20, 25, 30)] + [(20, K) for K in (2, 3, 4, 5, 6, 7)]
+    rows = []
+    for prof in ("box", "gauss"):
+        for S, K in points:
+            h = api.snlm_default_h(a.sigma, K, prof)
+
+            def step():
+                api.snlm_denoise_ws(img, S, K, h, prof, a.order, a.sigma, out=out, workspace=ws, stream=stream)
+
+            for _ in range(3):
+                step()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.median([e0.elapsed_time(e1) for e0, e1 in evs]))
+            rows.append({"profile": prof, "S": S, "K": K, "ms": ms, "Mpixel_s": n * n / (ms * 1e-3) / 1e6})
+    print(json.dumps({"sweep": "Alg. 4 run time against S and K", "size": n, "dtype": a.dtype, "order": a.order,
+                      "rows": rows}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.sweep:
+        run_sweep(a)
     else:
         run_ours(a)
 

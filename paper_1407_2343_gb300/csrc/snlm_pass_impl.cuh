@@ -998,12 +998,19 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
 
 // CTAs per SM the compiler is held to (registers per thread = 65536 / (128 x this)),
 // chosen per variant by measurement on GB300: the plain running-sum pass is fastest
-// at 5 (96 registers), the float and SURE passes at 4 (128 registers, no spills).
-template <int DM, bool SURE>
-constexpr int pass_min_ctas() { return (SURE || DM != DIST_SLIDE) ? 4 : 5; }
+// at 5 (96 registers) up to K = 5 and at 4 beyond (96 registers spill there); the
+// float and SURE passes at 4 (128 registers), the SURE passes at 3 (168 registers)
+// from K = 7, where 128 registers spill (21 % faster at 4096^2, S = 20).
+template <int K, int DM, bool SURE>
+constexpr int pass_min_ctas()
+{
+    if (SURE)
+        return K >= 7 ? 3 : 4;
+    return (DM != DIST_SLIDE || K >= 6) ? 4 : 5;
+}
 
 template <int K, int DM, bool SURE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<DM, SURE>()) nlm_pass_kernel(const __grid_constant__ PassArgs p)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<K, DM, SURE>()) nlm_pass_kernel(const __grid_constant__ PassArgs p)
 {
     extern __shared__ __align__(16) float smem[];
     process_tile<K, DM, SURE>(p, (int)blockIdx.x, smem);
