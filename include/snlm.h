@@ -141,8 +141,8 @@ int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host
  * approximation of the range kernel.
  *   in   DEVICE float32, H rows of in_pitch >= W elements.
  *   out  DEVICE float32, H rows of out_pitch >= W elements; must not overlap in.
- *   sigma_s > 0, sigma_r > 0, both finite; R <= 8 (sigma_s < 3), else
- *   SNLM_ERR_UNSUPPORTED. Asynchronous on `stream`.
+ *   sigma_s > 0, sigma_r > 0, both finite; R <= 8 (sigma_s < 3) and H <= 1,048,560,
+ *   else SNLM_ERR_UNSUPPORTED. Asynchronous on `stream`.
  */
 int snlm_bilateral(const float *in, int H, int W, int in_pitch, float sigma_s, float sigma_r, float *out,
                    int out_pitch, void *stream);
@@ -175,7 +175,7 @@ int snlm_denoise_bf(const void *img, int dtype, int H, int W, int pitch, int S, 
  * through the half-sample symmetric extension along each axis. Evaluated exactly
  * (every offset of the window, the patch sum as two 1-D filters), FP32.
  *   img  DEVICE, H rows of `pitch` elements of `dtype`; out DEVICE float32 H x W.
- *   S <= 32 and K <= 7 (else SNLM_ERR_UNSUPPORTED). Asynchronous on `stream`.
+ *   S <= 32, K <= 7 and H <= 1,048,560 (else SNLM_ERR_UNSUPPORTED). Asynchronous on `stream`.
  */
 int snlm_nlm_2d(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
                 float alpha, float *out, void *stream);

@@ -265,8 +265,8 @@ int check_bilateral(const float *in, int H, int W, long long in_pitch, float sig
         return SNLM_ERR_ARG;
     if (!(sigma_s > 0.f) || !std::isfinite(sigma_s) || !(sigma_r > 0.f) || !std::isfinite(sigma_r))
         return SNLM_ERR_ARG;
-    if (bilateral_radius(sigma_s) > kBfMaxR)
-        return SNLM_ERR_UNSUPPORTED;
+    if (bilateral_radius(sigma_s) > kBfMaxR || div_up(H, kBfTileH) > 65535)
+        return SNLM_ERR_UNSUPPORTED;                    // (the grid's y extent holds the row tiles)
     if (!is_device_ptr(in) || !is_device_ptr(out))
         return SNLM_ERR_ARG;
     if (overlaps(in, (long long)(H - 1) * in_pitch + W, out, (long long)(H - 1) * out_pitch + W))

@@ -203,8 +203,8 @@ extern "C" int snlm_nlm_2d(const void *img, int dtype, int H, int W, int pitch, 
         return SNLM_ERR_ARG;
     if (!(h > 0.f) || !std::isfinite(h))
         return SNLM_ERR_ARG;
-    if (S > kMaxS2d || K > kMaxK)
-        return SNLM_ERR_UNSUPPORTED;
+    if (S > kMaxS2d || K > kMaxK || div_up(H, kN2Ty) > 65535)
+        return SNLM_ERR_UNSUPPORTED;                    // (the grid's y extent holds the row tiles)
     if (!is_device_ptr(img) || !is_device_ptr(out))
         return SNLM_ERR_ARG;
     Nlm2dArgs a;
