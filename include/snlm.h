@@ -141,7 +141,7 @@ int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host
  * approximation of the range kernel.
  *   in   DEVICE float32, H rows of in_pitch >= W elements.
  *   out  DEVICE float32, H rows of out_pitch >= W elements; must not overlap in.
- *   sigma_s > 0, sigma_r > 0, both finite; R <= 8 (sigma_s < 3) and H <= 1,048,560,
+ *   sigma_s > 0, sigma_r > 0, both finite; R <= 8 (sigma_s < 3) and H <= 2,097,120,
  *   else SNLM_ERR_UNSUPPORTED. Asynchronous on `stream`.
  */
 int snlm_bilateral(const float *in, int H, int W, int in_pitch, float sigma_s, float sigma_r, float *out,

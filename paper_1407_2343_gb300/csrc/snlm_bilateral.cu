@@ -12,9 +12,9 @@
 // bank) and cr = -log2(e) / (2 sigma_r^2). The result is formed in centred form,
 // f~(i) + sum w g t / sum w g with t = f~(i - j) - f~(i); the centre tap is 1.
 //
-// A CTA filters a 128 x 16 tile: it stages the tile with its R-wide halo in shared
+// A CTA filters a 128 x 32 tile: it stages the tile with its R-wide halo in shared
 // memory (reflected at the image borders), then each thread filters 4 consecutive
-// pixels of 2 rows, reading each window row with 16-byte shared-memory loads and
+// pixels of 4 rows, reading each window row with 16-byte shared-memory loads and
 // treating its pixels in pairs with packed FP32x2 arithmetic (the ex2 stays scalar).
 #include "snlm_host.h"
 #include "snlm_internal.h"
@@ -26,7 +26,7 @@ namespace {
 constexpr int kBfPx = 4;                      // consecutive pixels of a row per thread
 constexpr int kBfTileW = 32 * kBfPx;          // columns per CTA
 constexpr int kBfWarps = 8;
-constexpr int kBfRowsPerThread = 2;
+constexpr int kBfRowsPerThread = 4;
 constexpr int kBfTileH = kBfWarps * kBfRowsPerThread;
 constexpr int kBfTaps = (2 * kBfMaxR + 1) * (2 * kBfMaxR + 1);
 
