@@ -43,7 +43,8 @@ typedef enum {
     SNLM_ERR_CUDA = -2,        /* a CUDA call failed (launch, copy, or a sticky device error) */
     SNLM_ERR_NOMEM = -3,       /* device or host memory could not be obtained */
     SNLM_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
-    SNLM_ERR_UNSUPPORTED = -5  /* valid request outside the compiled configurations */
+    SNLM_ERR_UNSUPPORTED = -5, /* valid request outside the compiled configurations */
+    SNLM_ERR_CHECK = -6        /* checked builds only: a kernel wrote past its shared-memory rows */
 } snlm_status;
 
 typedef enum { SNLM_U8 = 0, SNLM_F16 = 1, SNLM_F32 = 2 } snlm_dtype;

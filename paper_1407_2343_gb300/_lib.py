@@ -11,7 +11,8 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libsnlm.so")
+# SNLM_LIBRARY selects another build of the library (the checked build in tests)
+LIB_PATH = os.environ.get("SNLM_LIBRARY") or os.path.join(_PKG, "libsnlm.so")
 
 _lock = threading.Lock()
 _lib = None

@@ -283,6 +283,7 @@ const char *snlm_status_str(int status)
     case SNLM_ERR_NOMEM: return "SNLM_ERR_NOMEM: out of memory";
     case SNLM_ERR_TIMEOUT: return "SNLM_ERR_TIMEOUT: a bounded device wait gave up";
     case SNLM_ERR_UNSUPPORTED: return "SNLM_ERR_UNSUPPORTED: configuration not compiled";
+    case SNLM_ERR_CHECK: return "SNLM_ERR_CHECK: a shared-memory guard was overwritten (checked build)";
     default: return "SNLM: unknown status";
     }
 }

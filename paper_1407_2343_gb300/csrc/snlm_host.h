@@ -9,6 +9,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/snlm.h"
 #include "snlm_internal.h"
 
@@ -135,7 +137,9 @@ inline cudaEvent_t trace_event(Trace &t)
     return e;
 }
 
-// Brackets one launch with events when tracing is on.
+// Brackets one launch with an NVTX range named after its kind (so that profilers
+// can select a pass, e.g. ncu --nvtx --nvtx-include "row_pass_sure/block/") and,
+// when tracing is on, with events on its stream.
 struct TraceScope {
     int kind;
     cudaStream_t st;
@@ -143,6 +147,7 @@ struct TraceScope {
     bool active = false;
     TraceScope(int k, cudaStream_t s) : kind(k), st(s)
     {
+        nvtxRangePushA(snlm_kernel_name(k));
         Trace &t = trace();
         std::lock_guard<std::mutex> g(t.mu);
         if (!t.on)
@@ -154,6 +159,7 @@ struct TraceScope {
     }
     ~TraceScope()
     {
+        nvtxRangePop();
         if (!active)
             return;
         Trace &t = trace();

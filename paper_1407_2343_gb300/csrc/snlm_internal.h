@@ -14,6 +14,14 @@ constexpr int kMaxS2d = 32;        // largest search half-width of the 2-D NLM
 constexpr int kRun = 8;            // consecutive positions a lane owns (M)
 constexpr int kWarpsPerCta = 4;    // lines per CTA (one warp per line tile)
 constexpr int kPartials = 8;       // doubles per CTA in the SURE partial-sum records
+#ifdef SNLM_CHECKED
+// Checked builds: guard words after each warp's shared-memory rows, written before a
+// unit's first store and verified after its last (SNLM_ERR_CHECK when damaged).
+constexpr int kSmemGuard = 8;
+#else
+constexpr int kSmemGuard = 0;
+#endif
+constexpr unsigned kGuardWord = 0x5a17c0deu;
 
 enum DType { DT_U8 = 0, DT_F16 = 1, DT_F32 = 2 };
 // How the patch distance of Eq. (3) is reduced along the line:
@@ -44,6 +52,7 @@ struct PassArgs {
     const float *delta_in;      // optional (SURE kernels): chained derivative in (NULL = 1)
     float *delta_out;           // optional (SURE kernels): chained derivative out
     double *partials;           // optional: kPartials sums per CTA (see below)
+    unsigned *check;            // checked builds: the device word a damaged guard is recorded in
     Lines aux_f;                // the noisy input image f, viewed like dst
     Lines aux_rc;               // f_rc (float32), viewed like dst: when given, the SURE sums below are formed
     // Per-CTA partial sums (SURE). With m = (f_rc + fhat)/2 and d = (f_rc - fhat)/2
@@ -68,6 +77,7 @@ struct WarpLayout {
     int LW;        // one stored-weight row (SURE, padded)
     int LT;        // one tile-sized row (blend, SURE delta in / out, f_rc, f; padded)
     int per_warp;  // total, multiple of 4
+    int guard;     // first of the kSmemGuard guard words (checked builds)
 };
 
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
@@ -89,7 +99,8 @@ __host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool 
         if (sure)                   // stored weights for |s| <= K; delta in, delta out; f_rc and f
             n += K * L.LW + 4 * L.LT;
     }
-    L.per_warp = (n + 3) & ~3;
+    L.guard = n;
+    L.per_warp = (n + kSmemGuard + 3) & ~3;
     return L;
 }
 
@@ -101,7 +112,15 @@ __host__ __device__ inline int tile_positions(int S)
 }
 
 // Fills the derived fields of a pass's arguments (after n_lines, N and S).
-inline void finish_pass_args(PassArgs &a) { a.tiles = div_up(a.N, tile_positions(a.S)); }
+// The device word of device-side failure records (snlm_tma_host.cu; read and
+// cleared by snlm_device_error).
+unsigned *device_error_word();
+
+inline void finish_pass_args(PassArgs &a)
+{
+    a.tiles = div_up(a.N, tile_positions(a.S));
+    a.check = kSmemGuard > 0 ? device_error_word() : nullptr;
+}
 
 template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
 
@@ -156,7 +175,6 @@ template <int K> cudaError_t pass_tma_occupancy(int dist_mode, bool sure, int sm
 bool plan_pass_tma(int K, const PassArgs &a, int dist_mode, bool sure, TmaPass *t, int *grid);
 cudaError_t launch_planned_tma(int K, const PassArgs &a, const TmaPass &t, int dist_mode, bool sure, int grid,
                                cudaStream_t st);
-unsigned *device_error_word();
 constexpr int kTraceTma = 1 << 12;   // trace-kind flag: the launch used the TMA kernel
 
 template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);

@@ -908,6 +908,11 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
     const WarpLayout L = warp_layout(S, K, SURE, false);
     const RowOffsets R(L, K);
     float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
+    if constexpr (kSmemGuard > 0) {
+        if (lane < kSmemGuard)
+            reinterpret_cast<unsigned *>(fl)[L.guard + lane] = kGuardWord ^ (unsigned)lane;
+        __syncthreads();
+    }
 
     // ---- load phase: the line windows (with reflection) and every tile input the
     // epilogue reads. The vector forms serve the common layouts; the scalar gathers
@@ -994,6 +999,13 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
         __syncwarp();
     }
     unit_epilogue<K, DM, SURE>(p, smem, L.per_warp, R, L.LW, bid, line0, xa, T, HR, have_line, fo, A, Q, A2);
+    if constexpr (kSmemGuard > 0) {
+        __syncthreads();
+        if (lane < kSmemGuard && p.check &&
+            reinterpret_cast<const unsigned *>(fl)[L.guard + lane] != (kGuardWord ^ (unsigned)lane))
+            atomicExch(p.check, (unsigned)(-SNLM_ERR_CHECK));
+        __syncthreads();
+    }
 }
 
 // CTAs per SM the compiler is held to (registers per thread = 65536 / (128 x this)),
