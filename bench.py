@@ -48,9 +48,9 @@ OPS_PER_PAIR = {"plain": 9, "sure": 11}
 # --no-cpu-baseline --no-rc --no-bf --no-nlm2d` (the first timed step's four
 # passes); valid only while the pass kernels' sources (PASS_KERNEL_SOURCES) hash to
 # `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "7d819b9d93eeafd0",
-           "bytes_per_launch": {"row_pass_sure/slide": 90.717696e6, "col_pass_sure/block": 178.725888e6,
-                                "col_pass_sure/slide": 96.91264e6, "row_pass_sure/block": 267.996672e6}}
+TRAFFIC = {"sources_sha": "b3a4cc4c39b91cf4",
+           "bytes_per_launch": {"row_pass_sure/slide": 91099136, "col_pass_sure/block": 179085824,
+                                "col_pass_sure/slide": 96861696, "row_pass_sure/block": 267706880}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
