@@ -562,15 +562,20 @@ int snlm_server_drain(snlm_server *s)
         if (err != SNLM_OK)
             break;
         if (!progress) {
-            // nothing to do until an arrival or a completion
-            double wait = 20e-6;
+            // Nothing to do until an arrival or a completion. With work in flight or
+            // queued, poll again after yielding the core: a timed sleep can overshoot
+            // by milliseconds on a loaded host, far longer than a launch takes. With
+            // the GPU idle and the queue empty, sleep until shortly before the next
+            // arrival, then poll.
+            const auto w0 = std::chrono::steady_clock::now();
+            double until = 0.0;
             if (s->queue.empty() && s->inflight.empty() && s->next < s->order.size())
-                wait = std::min(2e-3, s->reqs[s->order[s->next]].r.t_arrival - s->clock());
-            if (wait > 0) {
-                const auto w0 = std::chrono::steady_clock::now();
-                std::this_thread::sleep_for(std::chrono::duration<double>(wait));
-                idle += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
-            }
+                until = s->reqs[s->order[s->next]].r.t_arrival - s->clock();
+            if (until > 300e-6)
+                std::this_thread::sleep_for(std::chrono::duration<double>(std::min(2e-3, until - 200e-6)));
+            else
+                std::this_thread::yield();
+            idle += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
         }
     }
     if (err != SNLM_OK) {

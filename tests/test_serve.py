@@ -87,7 +87,9 @@ def test_admission_under_a_memory_cap(dev):
 
 @pytest.mark.gpu
 def test_native_server_results_alone_equal_results_in_the_mix(dev):
-    reqs = serve.make_schedule(48, rate=6000.0, seed=7, sizes=(128, 256, 512, 1024), weights=(0.4, 0.3, 0.2, 0.1))
+    # arrivals faster than the GPU serves them (a burst), so that requests queue up and
+    # share batch launches with each other
+    reqs = serve.make_schedule(48, rate=50000.0, seed=7, sizes=(128, 256, 512, 1024), weights=(0.4, 0.3, 0.2, 0.1))
     stats = serve.NativeServer("batched").run(reqs)
     assert stats.images == len(reqs)
     assert stats.max_batch > 1                         # small requests shared launches
