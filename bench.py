@@ -106,6 +106,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-bf", action="store_true", help="skip the bilateral post-filter measurement")
     ap.add_argument("--no-nlm2d", action="store_true", help="skip the 2-D NLM comparison")
+    ap.add_argument("--no-3d", action="store_true", help="skip the separable 3-D extension measurement")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -327,6 +328,37 @@ def measure_nlm2d(a, api, dev, stream, flush):
     return {"S": S, "K": K, "sigma": sigma, "dtype": a.dtype, "rows": rows,
             "note": "2-D NLM evaluated exactly on the GPU (every window offset, separable patch sum); "
                     "h = sigma * sqrt(sum of the patch kernel) for both methods"}
+
+
+def measure_3d(a, api, dev, stream, flush):
+    """The separable 3-D extension on a 256^3 volume (256 frames of the synthetic
+    scene at 256^2, the benchmark's storage type, S = 10, K = 3, box): device time
+    per call (all its launches, from the library's trace; L2 flushed between calls)
+    in the single order XYZ and the average of the six orders."""
+    import torch
+    from paper_1407_2343_gb300 import synth
+
+    n, S, K = 256, 10, 3
+    vol = np.stack([synth.scene(n, n, a.sigma, seed=300 + z).noisy for z in range(n)])
+    v = torch.from_numpy(synth.store(vol, a.dtype)).to(dev)
+    out = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    h = api.snlm_default_h(a.sigma, K)
+    res = {"volume": f"{n}^3 {a.dtype}", "S": S, "K": K}
+    for order in ("XYZ", "AVG6"):
+        api.snlm_denoise_3d(v, S, K, h, order3=order, out=out, stream=stream)
+        torch.cuda.synchronize()
+        reps = 5
+        api.snlm_trace_read()
+        api.snlm_trace_enable(True)
+        for _ in range(reps):
+            flush.zero_()
+            api.snlm_denoise_3d(v, S, K, h, order3=order, out=out, stream=stream)
+        torch.cuda.synchronize()
+        api.snlm_trace_enable(False)
+        tr = api.snlm_trace_read(1 << 16)
+        ms = sum(m for _, m in tr) / reps
+        res[order] = {"ms": ms, "Mvoxel_s": n ** 3 / (ms * 1e-3) / 1e6, "launches_per_call": len(tr) // reps}
+    return res
 
 
 def psnr(x, clean):
@@ -591,6 +623,9 @@ def run_ours(a):
 
     if not a.no_nlm2d and rank == 0:
         line["nlm_2d_comparison"] = measure_nlm2d(a, api, dev, stream, flush)
+
+    if not a.no_3d and rank == 0:
+        line["volume_3d"] = measure_3d(a, api, dev, stream, flush)
 
     if not a.no_batch:
         line["batched"] = measure_batched(a, dev, stream)

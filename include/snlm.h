@@ -182,6 +182,19 @@ int snlm_nlm_2d(const void *img, int dtype, int H, int W, int pitch, int S, int 
                 float alpha, float *out, void *stream);
 
 /*
+ * Separable 3-D extension (the paper's conclusion: separable NLM extends directly to
+ * video and volume data): the 1-D pass of Eq. (4) along x, y and z in turn.
+ *   vol   DEVICE, D x H x W samples of `dtype`, dense (x fastest, then y, then z).
+ *   out   DEVICE float32, D x H x W dense.
+ *   order3  SNLM3_XYZ: x, then y, then z; SNLM3_AVG6: the average of the six orders.
+ * S, K, h, profile, beta as in snlm_denoise (h > 0 required); D*H*W < 2^31.
+ * Scratch: two float32 volumes from the library's pool. Asynchronous on `stream`.
+ */
+typedef enum { SNLM3_XYZ = 0, SNLM3_AVG6 = 1 } snlm_order3;
+int snlm_denoise_3d(const void *vol, int dtype, int D, int H, int W, int S, int K, float h, int profile,
+                    float beta, int order3, float *out, void *stream);
+
+/*
  * One 1-D NLM pass (Eq. (4)) over n_lines signals, with the derivative chain of
  * Eq. (24) when delta_out is given (the computation of Alg. 3).
  *   x          DEVICE, samples of type dtype; sample i of line l is at
@@ -317,7 +330,9 @@ typedef enum {
     SNLM_K_LINE_PASS = 8,      /* snlm_nlm_1d pass over arbitrary strided lines */
     SNLM_K_BATCH = 9,          /* one persistent batch kernel (one K class) */
     SNLM_K_BILATERAL = 10,     /* bilateral post-filter of Sec. III-B (Eq. (BF)) */
-    SNLM_K_NLM_2D = 11         /* the 2-D NLM of Eqs. (1)-(2) (comparison workload) */
+    SNLM_K_NLM_2D = 11,        /* the 2-D NLM of Eqs. (1)-(2) (comparison workload) */
+    SNLM_K_LINE_PASS_3D = 12,  /* a 1-D pass of the separable 3-D extension */
+    SNLM_K_RELAYOUT_3D = 13    /* the 3-D extension's outer-dimension swaps and averaging */
 } snlm_kernel_kind;
 
 int snlm_trace_enable(int enable);

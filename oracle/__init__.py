@@ -18,6 +18,7 @@ Functions and the passages they follow:
   snlm           Alg. 4 with Eqs. (14), (19), (25); orders RC, CR, AVG, SURE
   snlm_parts     the intermediate images and derivative maps of Alg. 4
   nlm_2d         the 2-D non-local means of Eqs. (1)-(2) (the comparison workload)
+  snlm_3d        the separable 3-D extension: Eq. (4) along each axis of a volume in turn
   bf_params      sigma_s and sigma_r of the bilateral post-filter (Sec. IV-A)
   bilateral      the bilateral post-filter, Eq. (BF) of Sec. III-B
   snlm_full      SNLM[f]: Alg. 4 followed by the bilateral post-filter (Sec. III-B)
@@ -214,6 +215,25 @@ def nlm_2d(img, S, K, h: float, prof="box", alpha: float | None = None, nthreads
     if rc != 0:
         raise ValueError(f"oracle nlm_2d rejected its arguments (rc={rc})")
     return out
+
+
+def snlm_3d(vol, S: int, K: int, h: float, prof="box", beta: float | None = None, order="XYZ", nthreads: int = 0):
+    """The separable 3-D extension of a (D, H, W) volume: the 1-D NLM of Eq. (4)
+    along x (the last axis), y and z in the given order ("XYZ", any permutation of
+    the three letters, or "AVG6", the average of the six orders), each pass on the
+    previous pass's output."""
+    x = _f64(vol)
+    if order == "AVG6":
+        orders = ["XYZ", "XZY", "YXZ", "YZX", "ZXY", "ZYX"]
+        return sum(snlm_3d(x, S, K, h, prof, beta, o, nthreads) for o in orders) / 6.0
+    axis_of = {"X": 2, "Y": 1, "Z": 0}
+    for letter in order:
+        ax = axis_of[letter]
+        moved = np.moveaxis(x, ax, -1)
+        shp = moved.shape
+        f = nlm_1d(moved.reshape(-1, shp[-1]), S, K, h, prof, beta, nthreads=nthreads)
+        x = np.moveaxis(np.asarray(f).reshape(shp), -1, ax)
+    return np.ascontiguousarray(x)
 
 
 def default_h_2d(sigma: float, K: int, prof="box", alpha: float | None = None) -> float:

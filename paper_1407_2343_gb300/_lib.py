@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
         lib.snlm_denoise_bf.restype = ci
         lib.snlm_nlm_2d.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, cf, vp, vp]
         lib.snlm_nlm_2d.restype = ci
+        lib.snlm_denoise_3d.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, cf, ci, vp, vp]
+        lib.snlm_denoise_3d.restype = ci
         lib.snlm_nlm_1d.argtypes = [vp, ci, ci, ci, cll, cll, ci, ci, cf, ci, cf, vp, cll, cll, vp, vp, vp]
         lib.snlm_nlm_1d.restype = ci
         lib.snlm_patch_dist_1d.argtypes = [vp, ci, ci, ci, ci, ci, ci, ci, cf, vp, vp]
@@ -157,7 +159,7 @@ def load(build_if_missing: bool = False):
 EXPORTED = [
     "snlm_status_str", "snlm_version", "snlm_default_h", "snlm_workspace_bytes", "snlm_denoise",
     "snlm_denoise_ws", "snlm_denoise_host", "snlm_denoise_host_many", "snlm_bilateral", "snlm_bf_params",
-    "snlm_denoise_bf", "snlm_nlm_2d", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
+    "snlm_denoise_bf", "snlm_nlm_2d", "snlm_denoise_3d", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
     "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc", "snlm_batch_plan_create",
     "snlm_batch_plan_workspace_bytes", "snlm_batch_plan_upload", "snlm_batch_plan_launch",
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",

@@ -270,6 +270,29 @@ def snlm_nlm_2d(img, S: int, K: int, h: float, profile="box", alpha: float = 0.0
     return out
 
 
+ORDERS3 = {"XYZ": 0, "AVG6": 1}
+
+
+def snlm_denoise_3d(vol, S: int, K: int, h: float, profile="box", beta: float = 0.0, order3="XYZ", out=None,
+                    stream=None):
+    """Separable 3-D extension: the 1-D pass along x, y and z of a dense (D, H, W)
+    device tensor (uint8, float16 or float32); order3 "XYZ" or "AVG6" (the average
+    of the six orders). Returns out (float32, (D, H, W))."""
+    torch = _torch()
+    if vol.dim() != 3 or not vol.is_contiguous():
+        raise ValueError("vol must be a contiguous 3-D tensor (D, H, W)")
+    D, H, W = vol.shape
+    if out is None:
+        out = torch.empty((D, H, W), dtype=torch.float32, device=vol.device)
+    if out.shape != vol.shape or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor of vol's shape")
+    rc = _lib.load().snlm_denoise_3d(_ptr(vol), _dtype_code(vol), int(D), int(H), int(W), int(S), int(K), float(h),
+                                     _profile(profile), float(beta or 0.0), ORDERS3[order3] if isinstance(order3, str)
+                                     else int(order3), _ptr(out), _stream_ptr(stream))
+    _check(rc, "snlm_denoise_3d")
+    return out
+
+
 def snlm_nlm_1d(x, S: int, K: int, h: float, profile="box", beta: float = 0.0, fhat=None,
                 delta_in=None, delta_out=None, stream=None):
     """One 1-D NLM pass (Eq. (4)) over the rows of a 2-D device tensor `x`

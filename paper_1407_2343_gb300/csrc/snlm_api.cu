@@ -110,8 +110,9 @@ Pool &pool()
 
 // Returns scratch of at least `need` bytes on the current device, slot `slot`
 // (0: denoise scratch, 1 and 3: host-call inputs, 2 and 4: host-call outputs,
-// 5: the output of Alg. 4 before the bilateral post-filter).
-constexpr int kPoolSlots = 6;
+// 5: the output of Alg. 4 before the bilateral post-filter, 6 and 7: the volumes of
+// the 3-D extension).
+constexpr int kPoolSlots = 8;
 void *pool_get(size_t need, int slot)
 {
     int dev = 0;
@@ -497,6 +498,116 @@ int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host
     return snlm_device_error(st);
 }
 
+// One 1-D pass of the 3-D extension along `axis` (0: x, 1: y, 2: z) of a D x H x W
+// volume; dst has src's layout. Along x both orders of the volume, (z, y, x) and
+// (y, z, x), have lines of one stride; y needs the order (y, z, x) and z (z, y, x).
+static int pass_3d(const void *src, int dtype, float *dst, int D, int H, int W, int axis, int S, int K, float h,
+                   int profile, float beta, cudaStream_t st)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    long long ls, es;
+    int n, N;
+    if (axis == 0) {
+        n = D * H, N = W, ls = W, es = 1;
+    } else if (axis == 1) {
+        n = D * W, N = H, ls = 1, es = (long long)D * W;       // order (y, z, x)
+    } else {
+        n = H * W, N = D, ls = 1, es = (long long)H * W;       // order (z, y, x)
+    }
+    a.src = Lines{src, dtype, ls, es};
+    a.n_lines = n;
+    a.N = N;
+    a.S = S;
+    a.c2 = exp2_scale(h);
+    a.h2 = (float)((double)h * h);
+    fill_profile(a.g, K, profile, beta_or_default(beta, K));
+    a.dst = dst;
+    a.out_line_step = ls;
+    a.out_elem_step = es;
+    a.aux_f = Lines{nullptr, DT_F32, 0, 0};
+    a.aux_rc = Lines{nullptr, DT_F32, 0, 0};
+    finish_pass_args(a);
+    const int dm = dist_mode_for(dtype, profile);
+    TraceScope ts(SNLM_K_LINE_PASS_3D | (dm << 8), st);
+    return status_of(dispatch_pass(K, a, dm, false, st));
+}
+
+int snlm_denoise_3d(const void *vol, int dtype, int D, int H, int W, int S, int K, float h, int profile,
+                    float beta, int order3, float *out, void *stream)
+{
+    if (D < 1 || H < 1 || W < 1 || (long long)D * H * W >= (1LL << 31))
+        return SNLM_ERR_ARG;
+    if (S < 0 || S > kMaxS || K < 0 || !valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+        return SNLM_ERR_ARG;
+    if (!(h > 0.f) || !std::isfinite(h) || (order3 != SNLM3_XYZ && order3 != SNLM3_AVG6))
+        return SNLM_ERR_ARG;
+    if (K > kMaxK)
+        return SNLM_ERR_UNSUPPORTED;
+    if (!is_device_ptr(vol) || !is_device_ptr(out))
+        return SNLM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)D * H * W;
+    float *buf[2] = {static_cast<float *>(pool_get((size_t)n * sizeof(float), 6)),
+                     static_cast<float *>(pool_get((size_t)n * sizeof(float), 7))};
+    if (!buf[0] || !buf[1])
+        return SNLM_ERR_NOMEM;
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int n_orders = order3 == SNLM3_XYZ ? 1 : 6;
+    for (int o = 0; o < n_orders; ++o) {
+        // the samples in hand: the input itself (order (z, y, x), its own type) or a
+        // float32 volume in one of the two buffers
+        const void *cur = vol;
+        int cur_dt = dtype, lay = 0, cur_buf = -1;
+        auto next_buf = [&]() { return cur_buf == 0 ? 1 : 0; };
+        auto relayout = [&](int to) -> int {
+            const int b = next_buf();
+            // order 0 = D x H rows, order 1 = H x D rows (rows of W samples)
+            const cudaError_t e = to == 1 ? launch_swap_outer(cur, cur_dt, buf[b], H, D, W, st)
+                                          : launch_swap_outer(cur, cur_dt, buf[b], D, H, W, st);
+            cur = buf[b], cur_dt = DT_F32, lay = to, cur_buf = b;
+            return status_of(e);
+        };
+        for (int k = 0; k < 3; ++k) {
+            const int axis = perms[order3 == SNLM3_XYZ ? 0 : o][k];
+            int rc = SNLM_OK;
+            if (axis == 1 && lay != 1) {
+                TraceScope ts(SNLM_K_RELAYOUT_3D, st);
+                rc = relayout(1);
+            } else if (axis == 2 && lay != 0) {
+                TraceScope ts(SNLM_K_RELAYOUT_3D, st);
+                rc = relayout(0);
+            }
+            if (rc != SNLM_OK)
+                return rc;
+            // the last pass of the single order in order (z, y, x) writes the result
+            const bool last = k == 2 && n_orders == 1 && lay == 0;
+            const int b = next_buf();
+            float *dst = last ? out : buf[b];
+            rc = pass_3d(cur, cur_dt, dst, D, H, W, axis, S, K, h, profile, beta, st);
+            if (rc != SNLM_OK)
+                return rc;
+            if (last)
+                return SNLM_OK;
+            cur = dst, cur_dt = DT_F32, cur_buf = b;
+        }
+        if (lay == 1) {
+            TraceScope ts(SNLM_K_RELAYOUT_3D, st);
+            const int rc = n_orders == 1 ? status_of(launch_swap_outer(cur, DT_F32, out, D, H, W, st)) : relayout(0);
+            if (rc != SNLM_OK)
+                return rc;
+            if (n_orders == 1)
+                return SNLM_OK;
+        }
+        TraceScope ts(SNLM_K_RELAYOUT_3D, st);
+        const int rc = status_of(launch_axpby(static_cast<const float *>(cur), out, 1.f / 6.f, o == 0 ? 0.f : 1.f,
+                                              n, st));
+        if (rc != SNLM_OK)
+            return rc;
+    }
+    return SNLM_OK;
+}
+
 int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_step,
                 long long elem_step, int S, int K, float h, int profile, float beta, float *fhat,
                 long long out_line_step, long long out_elem_step, const float *delta_in,
@@ -615,7 +726,7 @@ const char *snlm_kernel_name(int kind)
 {
     // low byte: snlm_kernel_kind; bits 8..11: how the patch distances were
     // reduced; bit 12: the pass moved its data with TMA bulk tensor copies
-    static const char *names[12][4] = {
+    static const char *names[14][4] = {
         {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
         {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
         {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
@@ -628,6 +739,8 @@ const char *snlm_kernel_name(int kind)
         {"batch", "batch", "batch", "batch"},
         {"bilateral", "bilateral", "bilateral", "bilateral"},
         {"nlm_2d", "nlm_2d", "nlm_2d", "nlm_2d"},
+        {"line_pass_3d", "line_pass_3d/slide", "line_pass_3d/block", "line_pass_3d/fir"},
+        {"relayout_3d", "relayout_3d", "relayout_3d", "relayout_3d"},
     };
     static const char *tma_names[4][3] = {
         {"row_pass/slide/tma", "row_pass/block/tma", "row_pass/fir/tma"},
@@ -636,11 +749,11 @@ const char *snlm_kernel_name(int kind)
         {"col_pass_sure/slide/tma", "col_pass_sure/block/tma", "col_pass_sure/fir/tma"},
     };
     const int base = kind & 0xff, dm = (kind >> 8) & 0xf, tma = (kind >> 12) & 1;
-    if (kind < 0 || base > 11 || dm > 2 || (kind >> 13) != 0)
+    if (kind < 0 || base > 13 || dm > 2 || (kind >> 13) != 0)
         return "unknown";
     if (tma)
         return base <= 3 ? tma_names[base][dm] : "unknown";
-    const bool has_dm = base <= 3 || base == 7 || base == 8;
+    const bool has_dm = base <= 3 || base == 7 || base == 8 || base == 12;
     return names[base][has_dm ? dm + 1 : 0];
 }
 

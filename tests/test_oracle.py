@@ -526,3 +526,32 @@ def test_nlm_2d_gaussian_patch_kernel_is_the_2d_gaussian(orc):
             num += w * img[y + sy, x + sx]
             den += w
     assert abs(orc.nlm_2d(img, S, K, h, "gauss", alpha)[y, x] - num / den) < 1e-10
+
+
+# ---- the separable 3-D extension (Sec. V: separable NLM extends to volumes)
+
+def test_3d_extension_with_one_slice_is_the_rc_order(orc):
+    # along z a single slice is a signal of length 1, which every pass leaves as it is
+    img = synth.noisy_image(14, 19, 20.0, seed=21, dtype="u8").astype(np.float64)
+    S, K, h = 4, 2, 40.0
+    ref, _ = orc.snlm(img, S, K, h, order="RC")
+    got = orc.snlm_3d(img[None], S, K, h, order="XYZ")[0]
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-11)
+
+
+def test_3d_extension_axis_labels(orc):
+    # exchanging the x and z axes of the volume exchanges the roles of the passes
+    vol = np.random.default_rng(22).uniform(0, 255, (5, 6, 7))
+    S, K, h = 2, 1, 60.0
+    a = orc.snlm_3d(vol, S, K, h, order="XYZ")
+    b = orc.snlm_3d(np.ascontiguousarray(vol.transpose(2, 1, 0)), S, K, h, order="ZYX")
+    np.testing.assert_allclose(b.transpose(2, 1, 0), a, rtol=1e-13, atol=1e-11)
+    c = orc.snlm_3d(np.ascontiguousarray(vol.transpose(0, 2, 1)), S, K, h, order="YXZ")
+    np.testing.assert_allclose(c.transpose(0, 2, 1), a, rtol=1e-13, atol=1e-11)
+
+
+def test_3d_extension_constant_volume_and_average(orc):
+    assert np.abs(orc.snlm_3d(np.full((3, 4, 5), 12.5), 2, 1, 10.0, order="AVG6") - 12.5).max() < 1e-12
+    vol = np.random.default_rng(23).uniform(0, 255, (4, 5, 6))
+    avg = orc.snlm_3d(vol, 2, 1, 50.0, order="AVG6")
+    assert avg.min() >= vol.min() - 1e-9 and avg.max() <= vol.max() + 1e-9
