@@ -108,6 +108,12 @@ inline int status_of(cudaError_t e)
     return SNLM_ERR_CUDA;
 }
 
+// Separable 3-D extension (snlm_3d.cu): swap the two outer dimensions of a volume of
+// rows (out row (a, b) = in row (b, a), samples converted to float32), and
+// out = alpha x + beta out.
+cudaError_t launch_swap_outer(const void *in, int dtype, float *out, int A, int B, int W, cudaStream_t st);
+cudaError_t launch_axpby(const float *x, float *out, float alpha, float beta, long long n, cudaStream_t st);
+
 // ------------------------------------------------------------------ launch tracing
 
 struct TraceRec {

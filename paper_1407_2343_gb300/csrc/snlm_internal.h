@@ -124,12 +124,6 @@ inline void finish_pass_args(PassArgs &a)
 
 template <int K> cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st);
 
-// Separable 3-D extension (snlm_3d.cu): swap the two outer dimensions of a volume of
-// rows (out row (a, b) = in row (b, a), samples converted to float32), and
-// out = alpha x + beta out.
-cudaError_t launch_swap_outer(const void *in, int dtype, float *out, int A, int B, int W, cudaStream_t st);
-cudaError_t launch_axpby(const float *x, float *out, float alpha, float beta, long long n, cudaStream_t st);
-
 // Bilateral post-filter (snlm_bilateral.cu): argument checks (an snlm_status) and
 // the launch on validated arguments.
 int bilateral_radius(float sigma_s);
