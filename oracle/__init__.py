@@ -12,6 +12,10 @@ float64 by the caller; outputs are float64.
 Functions and the passages they follow:
   ext_index      half-sample symmetric extension (boundary reading, Sec. II)
   profile        g_beta of Sec. II (box or Gaussian, Eq. (3))
+  iir_coeffs     the recursive Gaussian of Young and van Vliet (1995) that Sec. II-B
+                 names for the constant-time Gaussian profile: B, b1/b0, b2/b0, b3/b0, q
+  iir_margin     samples outside a line at which its two passes start from rest
+  iir_filter     that filter (causal then anti-causal pass) of a finite sequence
   default_h      h = sigma * sqrt(sum_k g(k))
   patch_dist_1d  Eq. (3) for every i and every offset s in [-S, S]
   nlm_1d         Eq. (4) and, when asked, the divergence of Eq. (24) (Alg. 3)
@@ -37,10 +41,11 @@ _SRC = os.path.join(_HERE, "snlm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
-BOX, GAUSS = 0, 1
+BOX, GAUSS, GAUSS_IIR = 0, 1, 2
 RC, CR, AVG, SURE = 0, 1, 2, 3
 ORDERS = {"RC": RC, "CR": CR, "AVG": AVG, "SURE": SURE}
-PROFILES = {"box": BOX, "gauss": GAUSS, "BOX": BOX, "GAUSS": GAUSS}
+PROFILES = {"box": BOX, "gauss": GAUSS, "BOX": BOX, "GAUSS": GAUSS, "gauss_iir": GAUSS_IIR,
+            "GAUSS_IIR": GAUSS_IIR}
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +78,12 @@ def _load():
         lib.orc_profile.restype = None
         lib.orc_default_h.argtypes = [cd, ci, ci, cd]
         lib.orc_default_h.restype = cd
+        lib.orc_iir_coeffs.argtypes = [cd, dp]
+        lib.orc_iir_coeffs.restype = ci
+        lib.orc_iir_margin.argtypes = [cd]
+        lib.orc_iir_margin.restype = i64
+        lib.orc_iir_filter.argtypes = [dp, i64, cd, dp]
+        lib.orc_iir_filter.restype = ci
         lib.orc_patch_dist_1d.argtypes = [dp, i64, i64, ci, ci, ci, cd, dp, ci]
         lib.orc_patch_dist_1d.restype = ci
         lib.orc_nlm_1d.argtypes = [dp, i64, i64, ci, ci, cd, ci, cd, dp, dp, dp, ci]
@@ -128,6 +139,31 @@ def profile(K: int, prof="box", beta: float | None = None) -> np.ndarray:
     g = np.empty(2 * K + 1, np.float64)
     _load().orc_profile(K, _profile_id(prof), float(beta if beta is not None else default_beta(K)), _ptr(g))
     return g
+
+
+def iir_coeffs(beta: float) -> dict:
+    """Young-van Vliet coefficients for standard deviation beta (0.5 <= beta <= 64)."""
+    c = np.empty(5, np.float64)
+    if _load().orc_iir_coeffs(float(beta), _ptr(c)) != 0:
+        raise ValueError(f"recursive Gaussian needs 0.5 <= beta <= 64 (got {beta})")
+    return dict(zip(("B", "a1", "a2", "a3", "q"), c.tolist()))
+
+
+def iir_margin(beta: float) -> int:
+    m = int(_load().orc_iir_margin(float(beta)))
+    if m < 0:
+        raise ValueError(f"recursive Gaussian needs 0.5 <= beta <= 64 (got {beta})")
+    return m
+
+
+def iir_filter(x, beta: float) -> np.ndarray:
+    """The recursive Gaussian (causal, then anti-causal pass) of a 1-D sequence,
+    from a zero state outside it."""
+    xv = _f64(x).ravel()
+    y = np.empty_like(xv)
+    if _load().orc_iir_filter(_ptr(xv), xv.size, float(beta), _ptr(y)) != 0:
+        raise ValueError(f"recursive Gaussian needs 0.5 <= beta <= 64 (got {beta})")
+    return y
 
 
 def default_h(sigma: float, K: int, prof="box", beta: float | None = None) -> float:
@@ -189,13 +225,16 @@ def snlm(img, S: int, K: int, h: float, prof="box", beta: float | None = None, o
 
 
 def snlm_parts(img, S: int, K: int, h: float, prof="box", beta: float | None = None, nthreads: int = 0):
-    """The intermediate results of Alg. 4: dict with fr, frc, fc, fcr, d1, d2."""
+    """The intermediate results of Alg. 4: dict with fr, frc, fc, fcr, d1, d2 (no
+    d1, d2 for the recursive Gaussian profile, which has no divergence here)."""
     x = _f64(img)
     H, W = x.shape
-    parts = {k: np.empty_like(x) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")}
+    keys = ("fr", "frc", "fc", "fcr") if _profile_id(prof) == GAUSS_IIR else ("fr", "frc", "fc", "fcr", "d1", "d2")
+    parts = {k: np.empty_like(x) for k in keys}
     rc = _load().orc_snlm_parts(_ptr(x), H, W, S, K, float(h), _profile_id(prof),
                                 float(beta if beta is not None else default_beta(K)),
-                                *[_ptr(parts[k]) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")], _nt(nthreads))
+                                *[_ptr(parts.get(k)) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")],
+                                _nt(nthreads))
     if rc != 0:
         raise ValueError(f"oracle snlm_parts rejected its arguments (rc={rc})")
     return parts

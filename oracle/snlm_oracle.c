@@ -23,6 +23,16 @@
  *    also satisfy |j-i| <= K (the Appendix sums over the window only).
  *  - SURE solve: A theta = b with A from Eq. (19) and b from Eq. (25); when A is
  *    (numerically) singular the minimum-norm pseudo-inverse solution is used.
+ *  - Recursive Gaussian profile (the constant-time route to Eq. (3) that Sec. II-B
+ *    points to): the third-order recursive filter of Young and van Vliet (1995),
+ *    a causal pass followed by an anti-causal pass with the same coefficients,
+ *    applied along i to the lifted squares (f(i) - f(i+s))^2 of the extended
+ *    signal. That filter has unit DC gain and approximates the sampled Gaussian
+ *    of standard deviation beta divided by its integral, so the distance is its
+ *    output times beta*sqrt(2 pi), the integral of g_beta. Its support is
+ *    infinite: both passes start from a zero state far enough outside [0, N)
+ *    (iir_margin) that the truncated tail is below double rounding.
+ *    The divergence of Eq. (24) is not defined for this profile here.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (no fast-math).
  */
@@ -36,6 +46,7 @@
 
 #define ORC_BOX 0
 #define ORC_GAUSS 1
+#define ORC_GAUSS_IIR 2
 
 #define ORC_RC 0
 #define ORC_CR 1
@@ -63,11 +74,93 @@ void orc_profile(int K, int profile, double beta, double *g)
         g[k + K] = (profile == ORC_GAUSS) ? exp(-((double)k * k) / (2.0 * beta * beta)) : 1.0;
 }
 
+/* Coefficients of the recursive Gaussian of Young and van Vliet (1995) for the
+ * standard deviation beta, from their design rules (q from beta, then the
+ * normalised denominator b1/b0, b2/b0, b3/b0 and the gain B that makes the DC
+ * gain of each pass exactly one):
+ *   q  = 0.98711 beta - 0.96330                    for beta >= 2.5,
+ *   q  = 3.97156 - 4.14554 sqrt(1 - 0.26891 beta)  for 0.5 <= beta < 2.5,
+ *   b0 = 1.57825 + 2.44413 q + 1.4281 q^2 + 0.422205 q^3,
+ *   b1 = 2.44413 q + 2.85619 q^2 + 1.26661 q^3,
+ *   b2 = -(1.4281 q^2 + 1.26661 q^3),
+ *   b3 = 0.422205 q^3,
+ *   B  = 1 - (b1 + b2 + b3) / b0.
+ * c receives {B, b1/b0, b2/b0, b3/b0, q}. Returns -1 outside [0.5, 64]. */
+int orc_iir_coeffs(double beta, double *c)
+{
+    if (!(beta >= 0.5) || !(beta <= 64.0))
+        return -1;
+    const double q = beta >= 2.5 ? 0.98711 * beta - 0.96330 : 3.97156 - 4.14554 * sqrt(1.0 - 0.26891 * beta);
+    const double q2 = q * q, q3 = q2 * q;
+    const double b0 = 1.57825 + 2.44413 * q + 1.4281 * q2 + 0.422205 * q3;
+    const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
+    const double b2 = -(1.4281 * q2 + 1.26661 * q3);
+    const double b3 = 0.422205 * q3;
+    c[0] = 1.0 - (b1 + b2 + b3) / b0;
+    c[1] = b1 / b0;
+    c[2] = b2 / b0;
+    c[3] = b3 / b0;
+    c[4] = q;
+    return 0;
+}
+
+/* Number of samples before (after) the first (last) output at which the causal
+ * (anti-causal) pass starts from a zero state. For every beta in [0.5, 64] the
+ * largest pole modulus rho of the filter satisfies rho^(80 q + 64) < exp(-89), so
+ * the truncated tail lies far under double rounding. */
+int64_t orc_iir_margin(double beta)
+{
+    double c[5];
+    if (orc_iir_coeffs(beta, c) != 0)
+        return -1;
+    return (int64_t)ceil(80.0 * c[4]) + 64;
+}
+
+/* The Young-van Vliet filter of a finite sequence x[0..n) with a zero state
+ * before x[0] and after x[n-1]:
+ *   causal       w(m) = B x(m) + a1 w(m-1) + a2 w(m-2) + a3 w(m-3),
+ *   anti-causal  y(m) = B w(m) + a1 y(m+1) + a2 y(m+2) + a3 y(m+3),
+ * with (a1, a2, a3) = (b1, b2, b3) / b0. y may not alias x. */
+int orc_iir_filter(const double *x, int64_t n, double beta, double *y)
+{
+    double c[5];
+    if (n < 0 || orc_iir_coeffs(beta, c) != 0)
+        return -1;
+    const double B = c[0], a1 = c[1], a2 = c[2], a3 = c[3];
+    double w1 = 0.0, w2 = 0.0, w3 = 0.0;
+    for (int64_t m = 0; m < n; ++m) {
+        const double w = B * x[m] + a1 * w1 + a2 * w2 + a3 * w3;
+        y[m] = w;
+        w3 = w2;
+        w2 = w1;
+        w1 = w;
+    }
+    double y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int64_t m = n - 1; m >= 0; --m) {
+        const double v = B * y[m] + a1 * y1 + a2 * y2 + a3 * y3;
+        y[m] = v;
+        y3 = y2;
+        y2 = y1;
+        y1 = v;
+    }
+    return 0;
+}
+
+/* Scale that turns the unit-gain recursive filter into the profile g_beta of
+ * Eq. (3): the integral of exp(-x^2 / (2 beta^2)), beta sqrt(2 pi). */
+static double iir_scale(double beta) { return beta * sqrt(2.0 * acos(-1.0)); }
+
 /* Smoothing parameter rule used when the caller gives none:
- * h = sigma * sqrt(sum_k g(k)), which is sigma*sqrt(2K+1) for the box. */
+ * h = sigma * sqrt(sum_k g(k)), which is sigma*sqrt(2K+1) for the box and
+ * sigma*sqrt(beta sqrt(2 pi)) for the recursive Gaussian (unit DC gain times
+ * the scale above). */
 double orc_default_h(double sigma, int K, int profile, double beta)
 {
     double g[2 * 64 + 1];
+    if (profile == ORC_GAUSS_IIR) {
+        double c[5];
+        return orc_iir_coeffs(beta, c) == 0 ? sigma * sqrt(iir_scale(beta)) : -1.0;
+    }
     if (K > 64)
         return -1.0;
     orc_profile(K, profile, beta, g);
@@ -97,11 +190,56 @@ static double patch_dist2(const double *fe, int64_t i, int64_t j, int K, const d
     return d;
 }
 
+/* Distances of the recursive Gaussian profile for one line (n samples, element
+ * stride `stride`): dtab[i*(2S+1) + (s+S)], i in [0, n), s in [-S, S], is
+ * beta sqrt(2 pi) times the Young-van Vliet filter, along m, of the lifted
+ * sequence (fe(m) - fe(m+s))^2 of the extended signal, both passes started
+ * iir_margin(beta) samples outside [0, n). Returns -1 on a bad beta, -3 when out
+ * of memory. */
+static int iir_dist_table(const double *f, int64_t n, int64_t stride, int S, double beta, double *dtab)
+{
+    const int64_t M = orc_iir_margin(beta);
+    if (M < 0)
+        return -1;
+    const int64_t R = M + S, L = n + 2 * M;
+    double *fe = (double *)malloc(sizeof(double) * (size_t)(n + 2 * R));
+    double *xs = (double *)malloc(sizeof(double) * (size_t)L);
+    double *ys = (double *)malloc(sizeof(double) * (size_t)L);
+    if (!fe || !xs || !ys) {
+        free(fe); free(xs); free(ys);
+        return -3;
+    }
+    extend_line(f, n, stride, R, fe);
+    const double scale = iir_scale(beta);
+    for (int s = -S; s <= S; ++s) {
+        for (int64_t m = -M; m < n + M; ++m) {
+            const double a = fe[R + m] - fe[R + m + s];
+            xs[M + m] = a * a;
+        }
+        orc_iir_filter(xs, L, beta, ys);
+        for (int64_t i = 0; i < n; ++i)
+            dtab[i * (2 * S + 1) + (s + S)] = scale * ys[M + i];
+    }
+    free(fe); free(xs); free(ys);
+    return 0;
+}
+
 /* Patch distances of n_lines signals of length N (row-major, line after line):
  * out[(line*N + i)*(2S+1) + (s+S)] = d^2(i, i+s) of Eq. (3), s in [-S, S]. */
 int orc_patch_dist_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, int profile,
                       double beta, double *out, int nthreads)
 {
+    if (profile == ORC_GAUSS_IIR) {
+        if (N < 1 || S < 0 || n_lines < 0 || orc_iir_margin(beta) < 0)
+            return -1;
+        int rc = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(min : rc)
+        for (int64_t ln = 0; ln < n_lines; ++ln) {
+            int r = iir_dist_table(x + ln * N, N, 1, S, beta, out + ln * N * (2 * S + 1));
+            rc = r < rc ? r : rc;
+        }
+        return rc;
+    }
     if (N < 1 || S < 0 || K < 0 || K > 64 || n_lines < 0)
         return -1;
     double g[2 * 64 + 1];
@@ -127,8 +265,10 @@ int orc_patch_dist_1d(const double *x, int64_t n_lines, int64_t N, int S, int K,
  * with d^2 from Eq. (3). `din` may alias `dout`; either may be NULL together. */
 static void nlm_line(const double *f, int64_t N, int64_t stride, const double *din, double *fhat,
                      double *dout, int64_t ostride, int S, int K, double h, const double *g,
-                     double *fe /* scratch, N + 2(S+K) */)
+                     const double *dtab, double *fe /* scratch, N + 2(S+K) */)
 {
+    /* dtab (recursive Gaussian profile only): the distances of iir_dist_table,
+     * used in place of the (2K+1)-tap sums; dout is NULL then. */
     const int64_t R = (int64_t)S + K;
     extend_line(f, N, stride, R, fe);
     const double h2 = h * h;
@@ -137,7 +277,8 @@ static void nlm_line(const double *f, int64_t N, int64_t stride, const double *d
         const int64_t ci = R + i;
         double W = 0.0, P1 = 0.0, P2 = 0.0;
         for (int s = -S; s <= S; ++s) {
-            double w = exp(-patch_dist2(fe, ci, ci + s, K, g) / h2);
+            const double d2 = dtab ? dtab[i * (2 * S + 1) + (s + S)] : patch_dist2(fe, ci, ci + s, K, g);
+            double w = exp(-d2 / h2);
             double fj = fe[ci + s];
             W += w;
             P1 += w * fj;
@@ -167,36 +308,60 @@ int orc_nlm_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, double
 {
     if (N < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0) || n_lines < 0)
         return -1;
+    const int iir = profile == ORC_GAUSS_IIR;
+    if (iir && orc_iir_margin(beta) < 0)
+        return -1;
+    if (iir && delta_out)
+        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
     const int64_t L = N + 2 * ((int64_t)S + K);
-#pragma omp parallel for schedule(static) num_threads(nthreads)
+    int rc = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(min : rc)
     for (int64_t ln = 0; ln < n_lines; ++ln) {
         double *fe = (double *)malloc(sizeof(double) * (size_t)L);
-        nlm_line(x + ln * N, N, 1, delta_in ? delta_in + ln * N : NULL, fhat + ln * N,
-                 delta_out ? delta_out + ln * N : NULL, 1, S, K, h, g, fe);
+        double *dtab = iir ? (double *)malloc(sizeof(double) * (size_t)(N * (2 * S + 1))) : NULL;
+        int r = (!fe || (iir && !dtab)) ? -3 : 0;
+        if (r == 0 && iir)
+            r = iir_dist_table(x + ln * N, N, 1, S, beta, dtab);
+        if (r == 0)
+            nlm_line(x + ln * N, N, 1, delta_in ? delta_in + ln * N : NULL, fhat + ln * N,
+                     delta_out ? delta_out + ln * N : NULL, 1, S, K, h, g, dtab, fe);
+        rc = r < rc ? r : rc;
         free(fe);
+        free(dtab);
     }
-    return 0;
+    return rc;
 }
 
 /* Apply the 1-D map to every row (axis 0) or every column (axis 1) of an H x W
  * row-major image; the derivative sequence is chained in place (Alg. 4). */
-static void sweep(const double *src, double *dst, double *delta, int64_t H, int64_t W, int axis,
-                  int S, int K, double h, const double *g, int nthreads)
+static int sweep(const double *src, double *dst, double *delta, int64_t H, int64_t W, int axis,
+                 int S, int K, double h, const double *g, int profile, double beta, int nthreads)
 {
     const int64_t n_lines = axis == 0 ? H : W;
     const int64_t N = axis == 0 ? W : H;
     const int64_t line_step = axis == 0 ? W : 1;
     const int64_t elem_step = axis == 0 ? 1 : W;
     const int64_t L = N + 2 * ((int64_t)S + K);
-#pragma omp parallel for schedule(static) num_threads(nthreads)
+    const int iir = profile == ORC_GAUSS_IIR;
+    int rc = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(min : rc)
     for (int64_t ln = 0; ln < n_lines; ++ln) {
         double *fe = (double *)malloc(sizeof(double) * (size_t)L);
-        nlm_line(src + ln * line_step, N, elem_step, delta ? delta + ln * line_step : NULL,
-                 dst + ln * line_step, delta ? delta + ln * line_step : NULL, elem_step, S, K, h, g, fe);
+        double *dtab = iir ? (double *)malloc(sizeof(double) * (size_t)(N * (2 * S + 1))) : NULL;
+        int r = (!fe || (iir && !dtab)) ? -3 : 0;
+        if (r == 0 && iir)
+            r = iir_dist_table(src + ln * line_step, N, elem_step, S, beta, dtab);
+        if (r == 0)
+            nlm_line(src + ln * line_step, N, elem_step, delta ? delta + ln * line_step : NULL,
+                     dst + ln * line_step, delta ? delta + ln * line_step : NULL, elem_step, S, K, h, g,
+                     dtab, fe);
+        rc = r < rc ? r : rc;
         free(fe);
+        free(dtab);
     }
+    return rc;
 }
 
 /* Minimum-norm solution of the symmetric 2x2 system [a c; c e] t = b.
@@ -252,6 +417,10 @@ int orc_snlm(const double *img, int64_t H, int64_t W, int S, int K, double h, in
         return -1;
     if (order == ORC_SURE && !(sigma >= 0.0))
         return -1;
+    if (profile == ORC_GAUSS_IIR && orc_iir_margin(beta) < 0)
+        return -1;
+    if (profile == ORC_GAUSS_IIR && order == ORC_SURE)
+        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
     const int64_t n = H * W;
@@ -270,13 +439,20 @@ int orc_snlm(const double *img, int64_t H, int64_t W, int S, int K, double h, in
     if (need_div)
         for (int64_t p = 0; p < n; ++p)
             d1[p] = d2[p] = 1.0;
+    int rc = 0;
     if (need_rc) {
-        sweep(img, tmp, d1, H, W, 0, S, K, h, g, nthreads); /* f_r  */
-        sweep(tmp, frc, d1, H, W, 1, S, K, h, g, nthreads); /* f_rc */
+        rc = sweep(img, tmp, d1, H, W, 0, S, K, h, g, profile, beta, nthreads); /* f_r  */
+        if (rc == 0)
+            rc = sweep(tmp, frc, d1, H, W, 1, S, K, h, g, profile, beta, nthreads); /* f_rc */
     }
-    if (need_cr) {
-        sweep(img, tmp, d2, H, W, 1, S, K, h, g, nthreads); /* f_c  */
-        sweep(tmp, fcr, d2, H, W, 0, S, K, h, g, nthreads); /* f_cr */
+    if (need_cr && rc == 0) {
+        rc = sweep(img, tmp, d2, H, W, 1, S, K, h, g, profile, beta, nthreads); /* f_c  */
+        if (rc == 0)
+            rc = sweep(tmp, fcr, d2, H, W, 0, S, K, h, g, profile, beta, nthreads); /* f_cr */
+    }
+    if (rc != 0) {
+        free(tmp); free(frc); free(fcr); free(d1); free(d2);
+        return rc;
     }
     double th[2] = {0.0, 0.0};
     double A11 = 0, A12 = 0, A22 = 0, Bf1 = 0, Bf2 = 0, Sd1 = 0, Sd2 = 0;
@@ -325,6 +501,11 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
 {
     if (H < 1 || W < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0))
         return -1;
+    const int iir = profile == ORC_GAUSS_IIR;
+    if (iir && orc_iir_margin(beta) < 0)
+        return -1;
+    if (iir && (d1 || d2))
+        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
     const int64_t n = H * W;
@@ -338,18 +519,19 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
     }
     for (int64_t p = 0; p < n; ++p)
         da[p] = db[p] = 1.0;
-    sweep(img, a, da, H, W, 0, S, K, h, g, nthreads);
+    double *pa = iir ? NULL : da, *pb = iir ? NULL : db; /* no divergence for the recursive profile */
+    int rc = sweep(img, a, pa, H, W, 0, S, K, h, g, profile, beta, nthreads);
     if (fr) memcpy(fr, a, sizeof(double) * (size_t)n);
-    sweep(a, b, da, H, W, 1, S, K, h, g, nthreads);
+    if (rc == 0) rc = sweep(a, b, pa, H, W, 1, S, K, h, g, profile, beta, nthreads);
     if (frc) memcpy(frc, b, sizeof(double) * (size_t)n);
     if (d1) memcpy(d1, da, sizeof(double) * (size_t)n);
-    sweep(img, a, db, H, W, 1, S, K, h, g, nthreads);
+    if (rc == 0) rc = sweep(img, a, pb, H, W, 1, S, K, h, g, profile, beta, nthreads);
     if (fc) memcpy(fc, a, sizeof(double) * (size_t)n);
-    sweep(a, b, db, H, W, 0, S, K, h, g, nthreads);
+    if (rc == 0) rc = sweep(a, b, pb, H, W, 0, S, K, h, g, profile, beta, nthreads);
     if (fcr) memcpy(fcr, b, sizeof(double) * (size_t)n);
     if (d2) memcpy(d2, db, sizeof(double) * (size_t)n);
     free(a); free(b); free(da); free(db);
-    return 0;
+    return rc;
 }
 
 /* Non-local means of Eqs. (1)-(2) (Sec. I), the comparison workload of the run-time
@@ -362,7 +544,8 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
 int orc_nlm_2d(const double *img, int64_t H, int64_t W, int Sy, int Sx, int Ky, int Kx, double h, int profile,
                double alpha, double *out, int nthreads)
 {
-    if (H < 1 || W < 1 || Sy < 0 || Sx < 0 || Ky < 0 || Kx < 0 || Ky > 64 || Kx > 64 || !(h > 0.0))
+    if (H < 1 || W < 1 || Sy < 0 || Sx < 0 || Ky < 0 || Kx < 0 || Ky > 64 || Kx > 64 || !(h > 0.0) ||
+        (profile != ORC_BOX && profile != ORC_GAUSS))
         return -1;
     double gy[2 * 64 + 1], gx[2 * 64 + 1];
     orc_profile(Ky, profile, alpha, gy);
