@@ -41,6 +41,10 @@ SFU_PEAK_TEXP = SMS * 32 * MAX_MHZ * 1e6 / 1e12
 # both pixels 4 (two FMA, two adds); the divergence passes add the weighted squared
 # differences of both pixels, 2 more. One MUFU ex2 per unique pair.
 OPS_PER_PAIR = {"plain": 9, "sure": 11}
+# The recursive Gaussian pass (Sec. II-B, Young-van Vliet filter): lift 2, causal
+# recursion 4 (B F + three taps), anti-causal recursion 4, exponent scale 1,
+# accumulation into both pixels 4; one ex2 per unique pair.
+OPS_PER_PAIR_IIR = 15
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # pass kernels of the 4096^2 u8 SURE step, from one ncu --set full capture of
@@ -107,6 +111,7 @@ def parse():
     ap.add_argument("--no-bf", action="store_true", help="skip the bilateral post-filter measurement")
     ap.add_argument("--no-nlm2d", action="store_true", help="skip the 2-D NLM comparison")
     ap.add_argument("--no-3d", action="store_true", help="skip the separable 3-D extension measurement")
+    ap.add_argument("--no-iir", action="store_true", help="skip the recursive Gaussian profile measurement")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -358,6 +363,63 @@ def measure_3d(a, api, dev, stream, flush):
         tr = api.snlm_trace_read(1 << 16)
         ms = sum(m for _, m in tr) / reps
         res[order] = {"ms": ms, "Mvoxel_s": n ** 3 / (ms * 1e-3) / 1e6, "launches_per_call": len(tr) // reps}
+    return res
+
+
+def measure_iir(a, api, dev, stream, flush):
+    """The recursive Gaussian profile (Sec. II-B) against the exact (2K+1)-tap
+    Gaussian of Eq. (3) on the benchmark's scene, AVG order (four passes, like
+    SURE, which this profile does not run): device time per call (from the
+    library's launch trace, L2 flushed between calls) at beta = K/2 for K = 2, 5
+    and 7, the roofline of the dominant recursive pass, and each output's PSNR
+    against the clean scene with their mean difference."""
+    import torch
+    from paper_1407_2343_gb300 import synth
+
+    sc = synth.scene(a.size, a.size, a.sigma, seed=0)
+    img = torch.from_numpy(synth.store(sc.noisy, a.dtype)).to(dev)
+    clean = torch.from_numpy(sc.clean.astype(np.float32)).to(dev)
+    out = torch.empty((a.size, a.size), dtype=torch.float32, device=dev)
+    ws = torch.empty(api.snlm_workspace_bytes(a.size, a.size, "AVG"), dtype=torch.uint8, device=dev)
+    px = a.size * a.size
+    res = {"order": "AVG", "S": a.S, "storage": a.dtype, "cases": []}
+    reps = 10
+    for K in (2, 5, 7):
+        beta = K / 2.0
+        case = {"K": K, "beta": beta}
+        outs = {}
+        for prof in ("gauss_iir", "gauss"):
+            h = api.snlm_default_h(a.sigma, K, prof, beta)
+            for _ in range(2):
+                api.snlm_denoise_ws(img, a.S, K, h, prof, "AVG", 0.0, beta, out=out, workspace=ws, stream=stream)
+            torch.cuda.synchronize()
+            api.snlm_trace_read()
+            api.snlm_trace_enable(True)
+            for _ in range(reps):
+                flush.zero_()
+                api.snlm_denoise_ws(img, a.S, K, h, prof, "AVG", 0.0, beta, out=out, workspace=ws, stream=stream)
+            torch.cuda.synchronize()
+            api.snlm_trace_enable(False)
+            tr = api.snlm_trace_read(1 << 16)
+            ms = sum(m for _, m in tr) / reps
+            outs[prof] = out.clone()
+            c = {"h": h, "ms": ms, "Mpixel_s": px / (ms * 1e-3) / 1e6,
+                 "psnr_db": float(10 * math.log10(255.0 ** 2 / float(((out - clean) ** 2).mean())))}
+            if prof == "gauss_iir":
+                per = {}
+                for name, m in tr:
+                    per.setdefault(name, []).append(m)
+                dom = max(per, key=lambda k: sum(per[k]))
+                avg_s = sum(per[dom]) / len(per[dom]) * 1e-3
+                pairs = px * a.S
+                ach = OPS_PER_PAIR_IIR * pairs / avg_s / 1e12
+                c["roofline"] = {"bound": "alu", "kernel": dom, "avg_launch_ms": avg_s * 1e3, "achieved": ach,
+                                 "peak": ALU_PEAK_TOPS, "unit": "Tops/s (FP32 lane-ops)", "frac": ach / ALU_PEAK_TOPS,
+                                 "ops_per_unique_pair": OPS_PER_PAIR_IIR, "unique_pairs_per_launch": pairs,
+                                 "sfu_frac": pairs / avg_s / 1e12 / SFU_PEAK_TEXP}
+            case[prof] = c
+        case["mean_abs_diff"] = float((outs["gauss_iir"] - outs["gauss"]).abs().mean())
+        res["cases"].append(case)
     return res
 
 
@@ -626,6 +688,9 @@ def run_ours(a):
 
     if not a.no_3d and rank == 0:
         line["volume_3d"] = measure_3d(a, api, dev, stream, flush)
+
+    if not a.no_iir and rank == 0:
+        line["gauss_iir"] = measure_iir(a, api, dev, stream, flush)
 
     if not a.no_batch:
         line["batched"] = measure_batched(a, dev, stream)

@@ -50,8 +50,18 @@ typedef enum {
 typedef enum { SNLM_U8 = 0, SNLM_F16 = 1, SNLM_F32 = 2 } snlm_dtype;
 
 /* Patch profile g_beta (Sec. II, Eq. (3)): box (g = 1) or Gaussian
- * g(k) = exp(-k^2 / (2 beta^2)), both truncated to k in [-K, K]. */
-typedef enum { SNLM_BOX = 0, SNLM_GAUSS = 1 } snlm_profile;
+ * g(k) = exp(-k^2 / (2 beta^2)), both truncated to k in [-K, K].
+ * SNLM_GAUSS_IIR is the recursive Gaussian that Sec. II-B names for computing the
+ * Gaussian distances in constant time per pair (the third-order filter of Young
+ * and van Vliet, 1995): the lifted squares (f(x) - f(x+s))^2 along each line go
+ * through its causal and anti-causal passes and are scaled by beta sqrt(2 pi), which
+ * approximates g_beta with infinite support (K then only sets the default beta =
+ * K/2). It needs 0.5 <= beta <= 3.5; results are float32 (not bit-exact). The plain
+ * entry points (snlm_denoise, _ws, _host, _host_many, _bf, _noalloc) accept it
+ * with the RC, CR and AVG orders; SURE, the batch plans, the server, the 2-D NLM and
+ * the 3-D extension return SNLM_ERR_UNSUPPORTED for it, and snlm_nlm_1d does when
+ * a derivative is asked. */
+typedef enum { SNLM_BOX = 0, SNLM_GAUSS = 1, SNLM_GAUSS_IIR = 2 } snlm_profile;
 
 /* How the row-then-column (RC) and column-then-row (CR) results are combined
  * (Sec. III, Eq. (14)): RC alone, CR alone, their average, or the SURE-optimal
@@ -65,7 +75,8 @@ const char *snlm_status_str(int status);
 int snlm_version(void);
 
 /* Default smoothing parameter h = sigma * sqrt(sum_{k=-K..K} g(k)); for the
- * box profile this is sigma * sqrt(2K+1). beta <= 0 selects beta = K/2.
+ * box profile this is sigma * sqrt(2K+1), for the recursive Gaussian
+ * sigma * sqrt(beta sqrt(2 pi)) (its whole response). beta <= 0 selects beta = K/2.
  * Returns -1 on an invalid argument. Host-only; no device work. */
 float snlm_default_h(float sigma, int K, int profile, float beta);
 
@@ -217,7 +228,9 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
  *         int32 when dtype == SNLM_U8 and profile == SNLM_BOX (exact integers),
  *         float32 otherwise.
  * Computed by the same device code as the fused passes: lifted squared
- * differences reduced by running sums (box) or the (2K+1)-tap profile (Gaussian).
+ * differences reduced by running sums (box), the (2K+1)-tap profile (Gaussian) or
+ * the recursive filter (SNLM_GAUSS_IIR, which writes d^2(i, i-s) from the filter
+ * of offset s by the band symmetry of Eq. (8)).
  */
 int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride, int S, int K,
                        int profile, float beta, void *out, void *stream);

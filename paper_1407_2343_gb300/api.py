@@ -14,13 +14,13 @@ import numpy as np
 from . import _lib
 
 U8, F16, F32 = 0, 1, 2
-BOX, GAUSS = 0, 1
+BOX, GAUSS, GAUSS_IIR = 0, 1, 2
 RC, CR, AVG, SURE = 0, 1, 2, 3
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_CHECK = 0, -1, -2, -3, -4, -5, -6
 MAX_K, MAX_S = 7, 128
 
 _ORDERS = {"RC": RC, "CR": CR, "AVG": AVG, "SURE": SURE}
-_PROFILES = {"box": BOX, "gauss": GAUSS}
+_PROFILES = {"box": BOX, "gauss": GAUSS, "gauss_iir": GAUSS_IIR}
 
 
 class SnlmError(RuntimeError):

@@ -178,6 +178,11 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     a.aux_rc = ps.aux_rc;
     finish_pass_args(a);
     const int dm = dist_mode_for(ps.src.dtype, profile);
+    if (dm == DIST_IIR) {
+        TraceScope ts((axis == 0 ? SNLM_K_ROW_PASS : SNLM_K_COL_PASS) | (dm << 8), st);
+        return run_iir_pass(a.src, a.n_lines, a.N, S, h, beta, a.dst, a.out_line_step, a.out_elem_step, a.blend,
+                            st);
+    }
     TmaPass t;
     int grid = 0;
     const bool tma = plan_pass_tma(K, a, dm, sure, &t, &grid);
@@ -293,9 +298,14 @@ int snlm_version(void) { return 100; }
 
 float snlm_default_h(float sigma, int K, int profile, float beta)
 {
-    if (!(sigma >= 0.f) || K < 0 || K > 64 || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+    if (!(sigma >= 0.f) || K < 0 || K > 64)
         return -1.f;
     const double bt = beta_or_default(beta, K);
+    if (profile == SNLM_GAUSS_IIR)   // unit DC gain times beta sqrt(2 pi)
+        return iir_check_beta(bt) == SNLM_OK ? (float)(sigma * sqrt(bt * sqrt(2.0 * 3.14159265358979323846)))
+                                             : -1.f;
+    if (profile != SNLM_BOX && profile != SNLM_GAUSS)
+        return -1.f;
     double s = 0.0;
     for (int k = -K; k <= K; ++k)
         s += profile == SNLM_GAUSS ? exp(-(double)k * k / (2.0 * bt * bt)) : 1.0;
@@ -313,7 +323,7 @@ int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, 
                     int profile, int order, float sigma, float beta, float *out, void *workspace,
                     size_t workspace_bytes, double *info, void *stream)
 {
-    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    int rc = check_denoise(H, W, S, K, h, profile, order, sigma, beta);
     if (rc != SNLM_OK)
         return rc;
     if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31))
@@ -333,7 +343,7 @@ int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, 
 int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
                  int profile, int order, float sigma, float beta, float *out, void *stream)
 {
-    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    int rc = check_denoise(H, W, S, K, h, profile, order, sigma, beta);
     if (rc != SNLM_OK)
         return rc;
     if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31))
@@ -355,7 +365,7 @@ int snlm_denoise_bf(const void *img, int dtype, int H, int W, int pitch, int S, 
         if (snlm_bf_params(sigma, &sigma_s, &sigma_r) != SNLM_OK || !(sigma_r > 0.f) || !(sigma_s > 0.f))
             return SNLM_ERR_ARG;
     }
-    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    int rc = check_denoise(H, W, S, K, h, profile, order, sigma, beta);
     if (rc != SNLM_OK)
         return rc;
     if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31) || !is_device_ptr(img))
@@ -379,7 +389,7 @@ int snlm_denoise_host(const void *img_host, int dtype, int H, int W, int pitch, 
                       float h, int profile, int order, float sigma, float beta, float *out_host,
                       void *stream)
 {
-    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    int rc = check_denoise(H, W, S, K, h, profile, order, sigma, beta);
     if (rc != SNLM_OK)
         return rc;
     if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31) || !img_host || !out_host)
@@ -412,7 +422,7 @@ int snlm_denoise_host_many(const void *const *imgs_host, float *const *outs_host
                            int W, int pitch, int S, int K, float h, int profile, int order, float sigma,
                            float beta, void *stream)
 {
-    int rc = check_common(H, W, S, K, h, profile, order, sigma);
+    int rc = check_denoise(H, W, S, K, h, profile, order, sigma, beta);
     if (rc != SNLM_OK)
         return rc;
     if (n < 0 || (n > 0 && (!imgs_host || !outs_host)) || !valid_dtype(dtype) || pitch < W ||
@@ -538,6 +548,8 @@ int snlm_denoise_3d(const void *vol, int dtype, int D, int H, int W, int S, int 
 {
     if (D < 1 || H < 1 || W < 1 || (long long)D * H * W >= (1LL << 31))
         return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR)
+        return SNLM_ERR_UNSUPPORTED;
     if (S < 0 || S > kMaxS || K < 0 || !valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
         return SNLM_ERR_ARG;
     if (!(h > 0.f) || !std::isfinite(h) || (order3 != SNLM3_XYZ && order3 != SNLM3_AVG6))
@@ -617,7 +629,12 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
         return SNLM_ERR_ARG;
     if (K > kMaxK)
         return SNLM_ERR_UNSUPPORTED;
-    if (!valid_dtype(dtype) || !(h > 0.f) || !isfinite(h) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+    if (!valid_dtype(dtype) || !(h > 0.f) || !isfinite(h) ||
+        (profile != SNLM_BOX && profile != SNLM_GAUSS && profile != SNLM_GAUSS_IIR))
+        return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR && (delta_in || delta_out))
+        return SNLM_ERR_UNSUPPORTED;
+    if (profile == SNLM_GAUSS_IIR && iir_check_beta(beta_or_default(beta, K)) != SNLM_OK)
         return SNLM_ERR_ARG;
     if (!is_device_ptr(x) || !is_device_ptr(fhat))
         return SNLM_ERR_ARG;
@@ -654,6 +671,9 @@ int snlm_nlm_1d(const void *x, int dtype, int n_lines, int N, long long line_ste
     finish_pass_args(a);
     const int dm = dist_mode_for(dtype, profile);
     TraceScope ts(SNLM_K_LINE_PASS | (dm << 8), static_cast<cudaStream_t>(stream));
+    if (dm == DIST_IIR)
+        return status_of(run_iir_pass(a.src, n_lines, N, S, h, beta_or_default(beta, K), fhat, out_line_step,
+                                      out_elem_step, nullptr, static_cast<cudaStream_t>(stream)));
     return status_of(dispatch_pass(K, a, dm, sure, static_cast<cudaStream_t>(stream)));
 }
 
@@ -668,10 +688,17 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
         return SNLM_ERR_ARG;
     if (K > kMaxK)
         return SNLM_ERR_UNSUPPORTED;
-    if (!valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
+    if (!valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS && profile != SNLM_GAUSS_IIR))
+        return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR && iir_check_beta(beta_or_default(beta, K)) != SNLM_OK)
         return SNLM_ERR_ARG;
     if (!is_device_ptr(x) || !is_device_ptr(out))
         return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR) {
+        TraceScope ts(SNLM_K_PATCH_DIST | (DIST_IIR << 8), static_cast<cudaStream_t>(stream));
+        return status_of(run_iir_dist(Lines{x, dtype, (long long)stride, 1}, n_lines, N, S, beta_or_default(beta, K),
+                                      static_cast<float *>(out), static_cast<cudaStream_t>(stream)));
+    }
     DistArgs a;
     memset(&a, 0, sizeof(a));
     a.src = Lines{x, dtype, (long long)stride, 1};
@@ -726,21 +753,21 @@ const char *snlm_kernel_name(int kind)
 {
     // low byte: snlm_kernel_kind; bits 8..11: how the patch distances were
     // reduced; bit 12: the pass moved its data with TMA bulk tensor copies
-    static const char *names[14][4] = {
-        {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir"},
-        {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir"},
-        {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir"},
-        {"col_pass_sure", "col_pass_sure/slide", "col_pass_sure/block", "col_pass_sure/fir"},
-        {"sure_solve", "sure_solve", "sure_solve", "sure_solve"},
-        {"combine", "combine", "combine", "combine"},
-        {"set_theta", "set_theta", "set_theta", "set_theta"},
-        {"patch_dist", "patch_dist/slide", "patch_dist/block", "patch_dist/fir"},
-        {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir"},
-        {"batch", "batch", "batch", "batch"},
-        {"bilateral", "bilateral", "bilateral", "bilateral"},
-        {"nlm_2d", "nlm_2d", "nlm_2d", "nlm_2d"},
-        {"line_pass_3d", "line_pass_3d/slide", "line_pass_3d/block", "line_pass_3d/fir"},
-        {"relayout_3d", "relayout_3d", "relayout_3d", "relayout_3d"},
+    static const char *names[14][5] = {
+        {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir", "row_pass/iir"},
+        {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir", "col_pass/iir"},
+        {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir", "unknown"},
+        {"col_pass_sure", "col_pass_sure/slide", "col_pass_sure/block", "col_pass_sure/fir", "unknown"},
+        {"sure_solve", "sure_solve", "sure_solve", "sure_solve", "sure_solve"},
+        {"combine", "combine", "combine", "combine", "combine"},
+        {"set_theta", "set_theta", "set_theta", "set_theta", "set_theta"},
+        {"patch_dist", "patch_dist/slide", "patch_dist/block", "patch_dist/fir", "patch_dist/iir"},
+        {"line_pass", "line_pass/slide", "line_pass/block", "line_pass/fir", "line_pass/iir"},
+        {"batch", "batch", "batch", "batch", "batch"},
+        {"bilateral", "bilateral", "bilateral", "bilateral", "bilateral"},
+        {"nlm_2d", "nlm_2d", "nlm_2d", "nlm_2d", "nlm_2d"},
+        {"line_pass_3d", "line_pass_3d/slide", "line_pass_3d/block", "line_pass_3d/fir", "unknown"},
+        {"relayout_3d", "relayout_3d", "relayout_3d", "relayout_3d", "relayout_3d"},
     };
     static const char *tma_names[4][3] = {
         {"row_pass/slide/tma", "row_pass/block/tma", "row_pass/fir/tma"},
@@ -749,10 +776,10 @@ const char *snlm_kernel_name(int kind)
         {"col_pass_sure/slide/tma", "col_pass_sure/block/tma", "col_pass_sure/fir/tma"},
     };
     const int base = kind & 0xff, dm = (kind >> 8) & 0xf, tma = (kind >> 12) & 1;
-    if (kind < 0 || base > 13 || dm > 2 || (kind >> 13) != 0)
+    if (kind < 0 || base > 13 || dm > 3 || (kind >> 13) != 0)
         return "unknown";
     if (tma)
-        return base <= 3 ? tma_names[base][dm] : "unknown";
+        return base <= 3 && dm <= 2 ? tma_names[base][dm] : "unknown";
     const bool has_dm = base <= 3 || base == 7 || base == 8 || base == 12;
     return names[base][has_dm ? dm + 1 : 0];
 }

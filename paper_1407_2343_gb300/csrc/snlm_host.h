@@ -56,6 +56,8 @@ inline float exp2_scale(double h)
 
 inline int dist_mode_for(int dtype, int profile)
 {
+    if (profile == SNLM_GAUSS_IIR)
+        return DIST_IIR;
     if (profile == SNLM_GAUSS)
         return DIST_FIR;
     return dtype == SNLM_U8 ? DIST_SLIDE : DIST_BLOCK;
@@ -79,6 +81,8 @@ inline int check_common(int H, int W, int S, int K, float h, int profile, int or
         return SNLM_ERR_UNSUPPORTED;
     if (!(h > 0.f) || !isfinite(h))
         return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR)
+        return SNLM_ERR_UNSUPPORTED;   // only the entry points that check with check_denoise run it
     if (profile != SNLM_BOX && profile != SNLM_GAUSS)
         return SNLM_ERR_ARG;
     if (order < SNLM_RC || order > SNLM_SURE)
@@ -91,6 +95,21 @@ inline int check_common(int H, int W, int S, int K, float h, int profile, int or
             return SNLM_ERR_ARG;
     }
     return SNLM_OK;
+}
+
+// check_common for the entry points that also run the recursive Gaussian profile:
+// beta (K/2 when beta <= 0) must lie in [kIirBetaMin, kIirBetaMax], and the SURE
+// order is not available with it (the divergence of Eq. (24) is not formed).
+inline int check_denoise(int H, int W, int S, int K, float h, int profile, int order, float sigma, float beta)
+{
+    if (profile != SNLM_GAUSS_IIR)
+        return check_common(H, W, S, K, h, profile, order, sigma);
+    const int rc = check_common(H, W, S, K, h, SNLM_GAUSS, order, sigma);
+    if (rc != SNLM_OK)
+        return rc;
+    if (order == SNLM_SURE)
+        return SNLM_ERR_UNSUPPORTED;
+    return iir_check_beta(beta_or_default(beta, K));
 }
 
 // view of a (pitched) image along rows (axis 0) or columns (axis 1)

@@ -1,0 +1,416 @@
+// Recursive Gaussian patch profile: the constant-time route to the Gaussian
+// distances of Eq. (3) that Sec. II-B names (the third-order recursive filter of
+// Young and van Vliet, 1995).
+//
+// For an offset s the distances d^2(x, x+s) along a line are the lifted squares
+// F(x) = (f(x+s) - f(x))^2 of the extended line, filtered by a causal pass
+//   w(x) = B F(x) + a1 w(x-1) + a2 w(x-2) + a3 w(x-3)
+// and then the same recursion run anti-causally on w, times beta sqrt(2 pi). The
+// filter has unit DC gain and approximates the normalised Gaussian of standard
+// deviation beta, so the product approximates the profile g_beta of Eq. (3) with
+// infinite support, at a cost per pair that does not depend on the patch width.
+//
+// Work decomposition. A CTA holds kIirWarps lines and one tile of output positions,
+// one warp per line; lane r owns the kIirRun = 16 consecutive positions
+// b0 + 16 r .. b0 + 16 r + 15 of a 512-position window. A recursion along the
+// window is spread over the lanes as a scan of affine maps (the parallel evaluation
+// of a linear recurrence): each lane runs the recursion over its own run from a zero
+// state, which gives the run's outputs w_loc and its end state v (the last three
+// outputs); the state entering lane r is sum_j A^(16 j) v_(r-1-j), formed by a
+// Kogge-Stone scan of warp shuffles with the 3x3 companion matrix A of the
+// recursion; each output then adds the response to that state, row 0 of A^(m+1)
+// times it. The anti-causal pass does the same from right to left.
+//
+// The impulse response decays geometrically, so a position needs a bounded history:
+// the host sets `halo` lanes on each side of the window, enough to cover the number
+// of samples after which the causal response stays below 1e-10 of its peak, and the
+// scan runs the rounds that reach that far (2^rounds >= halo). Outputs of the halo
+// lanes are discarded, and the S positions after the left halo only feed mirrored
+// pairs (below), so a tile has 16 (32 - 2 halo) - S output positions.
+//
+// Band symmetry (Eq. (8)): for the filter over the extended line,
+// d^2(x+s, -s) = d^2(x, s), so only s = 1..S are filtered. The weight of the pair
+// (x, x+s) goes to pixel x with the difference f(x+s) - f(x) and to pixel x+s with
+// the opposite one; the latter is read back from a per-warp shared-memory row that
+// holds the weights of the current offset. Accumulation is centred as in the
+// running-sum passes: fhat = f(x) + A / (1 + Q), A = sum w (f(j) - f(x)), Q = sum w.
+#include "snlm_host.h"
+#include "snlm_internal.h"
+
+#include <cuda_fp16.h>
+
+namespace snlm {
+
+namespace {
+
+constexpr int kIirRun = 16;                      // positions per lane
+constexpr int kIirSpan = 32 * kIirRun;           // positions per warp window
+constexpr int kIirWarps = 8;                     // lines per CTA
+constexpr int kIirMaxHalo = 4;                   // halo lanes per side (beta <= 3.5)
+constexpr int kIirMaxRounds = 2;                 // scan rounds (2^rounds >= halo)
+
+__host__ __device__ constexpr int iir_pad(int p) { return p + (p >> 4); }   // 32 lanes -> 32 banks
+
+constexpr int kIirLF = (iir_pad(kIirSpan + kMaxS) + 4) & ~3;   // line samples of a window
+constexpr int kIirLW = (iir_pad(kIirSpan) + 4) & ~3;           // weights of one offset
+constexpr int kIirPerWarp = kIirLF + kIirLW;
+
+struct IirArgs {
+    Lines src;
+    int n_lines, N, S;
+    int halo, rounds;            // halo lanes per side, scan rounds
+    int T;                       // output positions per tile
+    float B, a1, a2, a3;         // the recursion
+    float phi[kIirRun][3];       // row 0 of A^(m+1): response of output m to the entering state
+    float P[kIirMaxRounds][9];   // A^(16 * 2^d), row-major
+    float c2;                    // -log2(e) beta sqrt(2 pi) / h^2: w = 2^(c2 * filter output)
+    float scale;                 // beta sqrt(2 pi): distance = scale * filter output
+    float *dst;                  // fhat (pass) ...
+    long long out_line_step, out_elem_step;
+    const float *blend;          // optional: dst = (fhat + blend) / 2, indexed like dst
+    float *dist;                 // ... or the distances (n_lines, N, 2S+1), float32
+};
+
+// Half-sample symmetric extension of any x onto [0, n).
+__device__ __forceinline__ int iir_reflect(int x, int n)
+{
+    if (x >= 0 && x < n)
+        return x;
+    const int p = 2 * n;
+    int y = x % p;
+    if (y < 0)
+        y += p;
+    return y < n ? y : p - 1 - y;
+}
+
+// Element offsets fit in 31 bits (checked by the host before any launch).
+__device__ __forceinline__ float iir_load(const Lines &v, int line, int i)
+{
+    const unsigned off = (unsigned)(line * (int)v.line_step + i * (int)v.elem_step);
+    if (v.dtype == DT_U8)
+        return (float)__ldg(static_cast<const unsigned char *>(v.ptr) + off);
+    if (v.dtype == DT_F16)
+        return __half2float(__ldg(static_cast<const __half *>(v.ptr) + off));
+    return __ldg(static_cast<const float *>(v.ptr) + off);
+}
+
+__device__ __forceinline__ float iir_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// State entering each lane: the lanes' own end states (v0, v1, v2) combined over the
+// preceding lanes (UP) or the following lanes (down) by the Kogge-Stone scan
+// S_r <- S_r + A^(16 d) S_(r -+ d); the lane's entering state is its neighbour's S.
+template <bool UP>
+__device__ __forceinline__ void scan_state(float v0, float v1, float v2, const IirArgs &a, int lane, float &e0,
+                                           float &e1, float &e2)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    float s0 = v0, s1 = v1, s2 = v2;
+#pragma unroll
+    for (int d = 0; d < kIirMaxRounds; ++d) {
+        if (d < a.rounds) {
+            const int sh = 1 << d;
+            const float t0 = UP ? __shfl_up_sync(kAll, s0, sh) : __shfl_down_sync(kAll, s0, sh);
+            const float t1 = UP ? __shfl_up_sync(kAll, s1, sh) : __shfl_down_sync(kAll, s1, sh);
+            const float t2 = UP ? __shfl_up_sync(kAll, s2, sh) : __shfl_down_sync(kAll, s2, sh);
+            const bool has = UP ? lane >= sh : lane + sh < 32;
+            if (has) {
+                const float *P = a.P[d];
+                s0 = fmaf(P[0], t0, fmaf(P[1], t1, fmaf(P[2], t2, s0)));
+                s1 = fmaf(P[3], t0, fmaf(P[4], t1, fmaf(P[5], t2, s1)));
+                s2 = fmaf(P[6], t0, fmaf(P[7], t1, fmaf(P[8], t2, s2)));
+            }
+        }
+    }
+    e0 = UP ? __shfl_up_sync(kAll, s0, 1) : __shfl_down_sync(kAll, s0, 1);
+    e1 = UP ? __shfl_up_sync(kAll, s1, 1) : __shfl_down_sync(kAll, s1, 1);
+    e2 = UP ? __shfl_up_sync(kAll, s2, 1) : __shfl_down_sync(kAll, s2, 1);
+    if (UP ? lane == 0 : lane == 31)
+        e0 = e1 = e2 = 0.f;
+}
+
+// The recursive Gaussian of the lifted squares of one offset over the warp's window:
+// y[m] = filter output at position b0 + 16 lane + m (unscaled).
+__device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float (&y)[kIirRun], const IirArgs &a,
+                                               int lane)
+{
+    float w[kIirRun];
+    {
+        float w1 = 0.f, w2 = 0.f, w3 = 0.f;
+#pragma unroll
+        for (int m = 0; m < kIirRun; ++m) {
+            float v = fmaf(a.a3, w3, a.B * (dl[m] * dl[m]));
+            v = fmaf(a.a2, w2, v);
+            v = fmaf(a.a1, w1, v);
+            w[m] = v;
+            w3 = w2;
+            w2 = w1;
+            w1 = v;
+        }
+    }
+    float e0, e1, e2;
+    scan_state<true>(w[kIirRun - 1], w[kIirRun - 2], w[kIirRun - 3], a, lane, e0, e1, e2);
+#pragma unroll
+    for (int m = 0; m < kIirRun; ++m)
+        w[m] = fmaf(a.phi[m][0], e0, fmaf(a.phi[m][1], e1, fmaf(a.phi[m][2], e2, w[m])));
+    {
+        float y1 = 0.f, y2 = 0.f, y3 = 0.f;
+#pragma unroll
+        for (int m = kIirRun - 1; m >= 0; --m) {
+            float v = fmaf(a.a3, y3, a.B * w[m]);
+            v = fmaf(a.a2, y2, v);
+            v = fmaf(a.a1, y1, v);
+            y[m] = v;
+            y3 = y2;
+            y2 = y1;
+            y1 = v;
+        }
+    }
+    scan_state<false>(y[0], y[1], y[2], a, lane, e0, e1, e2);
+#pragma unroll
+    for (int m = 0; m < kIirRun; ++m) {
+        const int k = kIirRun - 1 - m;
+        y[m] = fmaf(a.phi[k][0], e0, fmaf(a.phi[k][1], e1, fmaf(a.phi[k][2], e2, y[m])));
+    }
+}
+
+// DIST = false: the 1-D NLM pass of Eq. (4) with the recursive profile.
+// DIST = true: the distances d^2(x, x+s), s in [-S, S], written to a.dist.
+template <bool DIST>
+__global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirArgs a)
+{
+    __shared__ __align__(16) float smem[kIirWarps * kIirPerWarp];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *fs = smem + warp * kIirPerWarp;       // f(b0 + q), q < kIirSpan + S
+    float *ws = fs + kIirLF;                     // weights of the current offset
+    const int q0 = a.halo * kIirRun + a.S;       // window index of the tile's first output
+    const int b0 = blockIdx.x * a.T - q0;        // line position of window index 0
+    const int base = lane * kIirRun;
+    const int nf = kIirSpan + a.S;
+    const int n_groups = div_up(a.n_lines, kIirWarps);
+    for (int grp = blockIdx.y; grp < n_groups; grp += gridDim.y) {
+        const int ln = grp * kIirWarps + warp;
+        if (ln >= a.n_lines)
+            continue;                            // warps work independently (no CTA barrier)
+        __syncwarp();
+        for (int q = lane; q < nf; q += 32)
+            fs[iir_pad(q)] = iir_load(a.src, ln, iir_reflect(b0 + q, a.N));
+        __syncwarp();
+        float fo[kIirRun], accA[kIirRun], accQ[kIirRun];
+#pragma unroll
+        for (int m = 0; m < kIirRun; ++m) {
+            fo[m] = fs[iir_pad(base + m)];
+            accA[m] = 0.f;
+            accQ[m] = 0.f;
+        }
+        for (int s = 1; s <= a.S; ++s) {
+            float dl[kIirRun], y[kIirRun];
+#pragma unroll
+            for (int m = 0; m < kIirRun; ++m)
+                dl[m] = fs[iir_pad(base + m + s)] - fo[m];
+            iir_filter_run(dl, y, a, lane);
+            if constexpr (DIST) {
+                const long long row = (long long)ln * a.N;
+                const int stride = 2 * a.S + 1;
+#pragma unroll
+                for (int m = 0; m < kIirRun; ++m) {
+                    const int q = base + m, x = b0 + q;
+                    const float d = a.scale * fmaxf(y[m], 0.f);   // the response is non-negative
+                    if (q >= q0 && q < q0 + a.T && x < a.N)
+                        a.dist[(row + x) * stride + a.S + s] = d;          // d^2(x, x+s)
+                    if (q + s >= q0 && q + s < q0 + a.T && x + s < a.N)
+                        a.dist[(row + x + s) * stride + a.S - s] = d;      // d^2(x+s, x)
+                }
+            } else {
+                float wt[kIirRun];
+#pragma unroll
+                for (int m = 0; m < kIirRun; ++m) {
+                    // the filter's response is non-negative, so a negative output is
+                    // float rounding of a zero distance (weight 1)
+                    wt[m] = iir_ex2(fminf(a.c2 * y[m], 0.f));
+                    accA[m] = fmaf(wt[m], dl[m], accA[m]);
+                    accQ[m] += wt[m];
+                    ws[iir_pad(base + m)] = wt[m];
+                }
+                __syncwarp();
+                // mirrored pairs: pixel q receives w(q - s, s) (f(q - s) - f(q)); window
+                // indices below 0 only occur in halo lanes, whose sums are discarded
+#pragma unroll
+                for (int m = 0; m < kIirRun; ++m) {
+                    const int q = max(base + m - s, 0);
+                    const float wm = ws[iir_pad(q)];
+                    accA[m] = fmaf(wm, fs[iir_pad(q)] - fo[m], accA[m]);
+                    accQ[m] += wm;
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kIirRun; ++m) {
+            const int q = base + m, x = b0 + q;
+            if (q < q0 || q >= q0 + a.T || x >= a.N)
+                continue;
+            if constexpr (DIST) {
+                a.dist[((long long)ln * a.N + x) * (2 * a.S + 1) + a.S] = 0.f;
+            } else {
+                float v = fo[m] + accA[m] / (1.f + accQ[m]);
+                const long long o = (long long)ln * a.out_line_step + (long long)x * a.out_elem_step;
+                if (a.blend)
+                    v = 0.5f * (v + a.blend[o]);
+                a.dst[o] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+// Young and van Vliet's design rules for standard deviation beta (0.5 <= beta):
+//   q  = 0.98711 beta - 0.96330 (beta >= 2.5), 3.97156 - 4.14554 sqrt(1 - 0.26891 beta) (below),
+//   b0 = 1.57825 + 2.44413 q + 1.4281 q^2 + 0.422205 q^3,  b1 = 2.44413 q + 2.85619 q^2 + 1.26661 q^3,
+//   b2 = -(1.4281 q^2 + 1.26661 q^3),  b3 = 0.422205 q^3,  B = 1 - (b1 + b2 + b3) / b0;
+// the recursion coefficients are a_k = b_k / b0.
+struct IirDesign {
+    double B, a[3];
+};
+
+IirDesign iir_design(double beta)
+{
+    const double q = beta >= 2.5 ? 0.98711 * beta - 0.96330 : 3.97156 - 4.14554 * sqrt(1.0 - 0.26891 * beta);
+    const double b0 = 1.57825 + q * (2.44413 + q * (1.4281 + q * 0.422205));
+    const double b1 = q * (2.44413 + q * (2.85619 + q * 1.26661));
+    const double b2 = -q * q * (1.4281 + q * 1.26661);
+    const double b3 = 0.422205 * q * q * q;
+    IirDesign d;
+    d.a[0] = b1 / b0;
+    d.a[1] = b2 / b0;
+    d.a[2] = b3 / b0;
+    d.B = 1.0 - (b1 + b2 + b3) / b0;
+    return d;
+}
+
+void mat3_mul(const double *x, const double *y, double *z)
+{
+    double t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            t[3 * i + j] = x[3 * i] * y[j] + x[3 * i + 1] * y[3 + j] + x[3 * i + 2] * y[6 + j];
+    memcpy(z, t, sizeof(t));
+}
+
+// Recursion, window geometry and scan tables of one call; SNLM_ERR_ARG when beta
+// is outside [kIirBetaMin, kIirBetaMax].
+int iir_plan(double beta, int S, IirArgs &a)
+{
+    if (!(beta >= kIirBetaMin && beta <= kIirBetaMax))
+        return SNLM_ERR_ARG;
+    const IirDesign d = iir_design(beta);
+    // samples after which the causal impulse response stays below 1e-10 of its peak
+    int warm = 0;
+    {
+        double w1 = 0, w2 = 0, w3 = 0, peak = 0;
+        for (int n = 0; n < 4096; ++n) {
+            const double v = (n == 0 ? d.B : 0.0) + d.a[0] * w1 + d.a[1] * w2 + d.a[2] * w3;
+            peak = fmax(peak, fabs(v));
+            if (fabs(v) > 1e-10 * peak)
+                warm = n + 1;
+            w3 = w2;
+            w2 = w1;
+            w1 = v;
+        }
+    }
+    a.halo = div_up(warm, kIirRun);
+    if (a.halo < 1)
+        a.halo = 1;
+    if (a.halo > kIirMaxHalo)
+        return SNLM_ERR_ARG;
+    a.rounds = 0;
+    while ((1 << a.rounds) < a.halo)
+        ++a.rounds;
+    a.T = kIirRun * (32 - 2 * a.halo) - S;
+    a.B = (float)d.B;
+    a.a1 = (float)d.a[0];
+    a.a2 = (float)d.a[1];
+    a.a3 = (float)d.a[2];
+    // companion matrix of the recursion: state (w(x), w(x-1), w(x-2))
+    const double A[9] = {d.a[0], d.a[1], d.a[2], 1, 0, 0, 0, 1, 0};
+    double Pm[9];
+    memcpy(Pm, A, sizeof(Pm));
+    for (int m = 0; m < kIirRun; ++m) {          // Pm = A^(m+1)
+        for (int c = 0; c < 3; ++c)
+            a.phi[m][c] = (float)Pm[c];
+        if (m + 1 < kIirRun)
+            mat3_mul(Pm, A, Pm);
+    }
+    double R[9];
+    mat3_mul(Pm, A, R);                          // A^16
+    for (int r = 0; r < kIirMaxRounds; ++r) {    // A^(16 * 2^r)
+        for (int c = 0; c < 9; ++c)
+            a.P[r][c] = (float)R[c];
+        mat3_mul(R, R, R);
+    }
+    a.scale = (float)(beta * sqrt(2.0 * 3.14159265358979323846));
+    return SNLM_OK;
+}
+
+cudaError_t launch_iir(const IirArgs &a, bool dist, cudaStream_t st)
+{
+    const int tiles = div_up(a.N, a.T);
+    const int groups = div_up(a.n_lines, kIirWarps);
+    const dim3 grid((unsigned)tiles, (unsigned)(groups < 65535 ? groups : 65535));
+    if (dist)
+        iir_pass_kernel<true><<<grid, kIirWarps * 32, 0, st>>>(a);
+    else
+        iir_pass_kernel<false><<<grid, kIirWarps * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int iir_check_beta(double beta)
+{
+    IirArgs a;
+    return iir_plan(beta, 0, a);
+}
+
+cudaError_t run_iir_pass(const Lines &src, int n_lines, int N, int S, double h, double beta, float *dst,
+                         long long out_line_step, long long out_elem_step, const float *blend, cudaStream_t st)
+{
+    IirArgs a;
+    memset(&a, 0, sizeof(a));
+    if (iir_plan(beta, S, a) != SNLM_OK)
+        return cudaErrorInvalidValue;
+    a.src = src;
+    a.n_lines = n_lines;
+    a.N = N;
+    a.S = S;
+    double c = -1.4426950408889634 * (double)a.scale / (h * h);
+    if (!(c > -3.0e38))
+        c = -3.0e38;
+    a.c2 = (float)c;
+    a.dst = dst;
+    a.out_line_step = out_line_step;
+    a.out_elem_step = out_elem_step;
+    a.blend = blend;
+    return launch_iir(a, false, st);
+}
+
+cudaError_t run_iir_dist(const Lines &src, int n_lines, int N, int S, double beta, float *out, cudaStream_t st)
+{
+    IirArgs a;
+    memset(&a, 0, sizeof(a));
+    if (iir_plan(beta, S, a) != SNLM_OK)
+        return cudaErrorInvalidValue;
+    a.src = src;
+    a.n_lines = n_lines;
+    a.N = N;
+    a.S = S;
+    a.dist = out;
+    return launch_iir(a, true, st);
+}
+
+}  // namespace snlm

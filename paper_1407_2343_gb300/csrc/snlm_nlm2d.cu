@@ -199,6 +199,8 @@ extern "C" int snlm_nlm_2d(const void *img, int dtype, int H, int W, int pitch, 
 {
     if (H < 1 || W < 1 || pitch < W || (long long)H * pitch >= (1LL << 31) || (long long)H * W >= (1LL << 31))
         return SNLM_ERR_ARG;
+    if (profile == SNLM_GAUSS_IIR)
+        return SNLM_ERR_UNSUPPORTED;
     if (S < 0 || K < 0 || !valid_dtype(dtype) || (profile != SNLM_BOX && profile != SNLM_GAUSS))
         return SNLM_ERR_ARG;
     if (!(h > 0.f) || !std::isfinite(h))
