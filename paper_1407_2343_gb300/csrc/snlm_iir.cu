@@ -60,11 +60,11 @@ struct IirArgs {
     int n_lines, N, S;
     int halo, rounds;            // halo lanes per side, scan rounds
     int T;                       // output positions per tile
-    float B, a1, a2, a3;         // the recursion
+    float a1, a2, a3;            // the recursion (its gain B is folded into c2 and scale)
     float phi[kIirRun][3];       // row 0 of A^(m+1): response of output m to the entering state
     float P[kIirMaxRounds][9];   // A^(16 * 2^d), row-major
-    float c2;                    // -log2(e) beta sqrt(2 pi) / h^2: w = 2^(c2 * filter output)
-    float scale;                 // beta sqrt(2 pi): distance = scale * filter output
+    float c2;                    // -log2(e) beta sqrt(2 pi) B^2 / h^2: w = 2^(c2 * y)
+    float scale;                 // beta sqrt(2 pi) B^2: distance = scale * y
     float *dst;                  // fhat (pass) ...
     long long out_line_step, out_elem_step;
     const float *blend;          // optional: dst = (fhat + blend) / 2, indexed like dst
@@ -134,7 +134,10 @@ __device__ __forceinline__ void scan_state(float v0, float v1, float v2, const I
 }
 
 // The recursive Gaussian of the lifted squares of one offset over the warp's window:
-// y[m] = filter output at position b0 + 16 lane + m (unscaled).
+// y[m] = filter output at position b0 + 16 lane + m divided by B^2. The gain B of
+// each pass is taken out of the recursions (u = w / B runs u(x) = F(x) + a1 u(x-1) +
+// a2 u(x-2) + a3 u(x-3), and y / B^2 the same recursion on u) and folded into the
+// host's distance scale and exponent factor, which saves one multiply per pass.
 __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float (&y)[kIirRun], const IirArgs &a,
                                                int lane)
 {
@@ -143,7 +146,7 @@ __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float
         float w1 = 0.f, w2 = 0.f, w3 = 0.f;
 #pragma unroll
         for (int m = 0; m < kIirRun; ++m) {
-            float v = fmaf(a.a3, w3, a.B * (dl[m] * dl[m]));
+            float v = fmaf(dl[m], dl[m], a.a3 * w3);
             v = fmaf(a.a2, w2, v);
             v = fmaf(a.a1, w1, v);
             w[m] = v;
@@ -161,7 +164,7 @@ __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float
         float y1 = 0.f, y2 = 0.f, y3 = 0.f;
 #pragma unroll
         for (int m = kIirRun - 1; m >= 0; --m) {
-            float v = fmaf(a.a3, y3, a.B * w[m]);
+            float v = fmaf(a.a3, y3, w[m]);
             v = fmaf(a.a2, y2, v);
             v = fmaf(a.a1, y1, v);
             y[m] = v;
@@ -332,7 +335,6 @@ int iir_plan(double beta, int S, IirArgs &a)
     while ((1 << a.rounds) < a.halo)
         ++a.rounds;
     a.T = kIirRun * (32 - 2 * a.halo) - S;
-    a.B = (float)d.B;
     a.a1 = (float)d.a[0];
     a.a2 = (float)d.a[1];
     a.a3 = (float)d.a[2];
@@ -347,13 +349,13 @@ int iir_plan(double beta, int S, IirArgs &a)
             mat3_mul(Pm, A, Pm);
     }
     double R[9];
-    mat3_mul(Pm, A, R);                          // A^16
+    memcpy(R, Pm, sizeof(R));                    // A^16: the transfer over one lane's run
     for (int r = 0; r < kIirMaxRounds; ++r) {    // A^(16 * 2^r)
         for (int c = 0; c < 9; ++c)
             a.P[r][c] = (float)R[c];
         mat3_mul(R, R, R);
     }
-    a.scale = (float)(beta * sqrt(2.0 * 3.14159265358979323846));
+    a.scale = (float)(beta * sqrt(2.0 * 3.14159265358979323846) * d.B * d.B);
     return SNLM_OK;
 }
 
@@ -388,7 +390,8 @@ cudaError_t run_iir_pass(const Lines &src, int n_lines, int N, int S, double h, 
     a.n_lines = n_lines;
     a.N = N;
     a.S = S;
-    double c = -1.4426950408889634 * (double)a.scale / (h * h);
+    const IirDesign d = iir_design(beta);
+    double c = -1.4426950408889634 * beta * sqrt(2.0 * 3.14159265358979323846) * d.B * d.B / (h * h);
     if (!(c > -3.0e38))
         c = -3.0e38;
     a.c2 = (float)c;
