@@ -22,18 +22,19 @@
 // times it. The anti-causal pass does the same from right to left.
 //
 // The impulse response decays geometrically, so a position needs a bounded history:
-// the host sets `halo` lanes on each side of the window, enough to cover the number
-// of samples after which the causal response stays below 1e-10 of its peak, and the
-// scan runs the rounds that reach that far (2^rounds >= halo). Outputs of the halo
-// lanes are discarded, and the S positions after the left halo only feed mirrored
-// pairs (below), so a tile has 16 (32 - 2 halo) - S output positions.
+// the host sets `warm`, the number of samples after which the causal response stays
+// below 1e-9 of its peak, and the scan runs the rounds that reach that far
+// (16 * 2^rounds >= warm). Only positions with `warm` samples of the window on both
+// sides have exact distances; the S positions after the first of them only feed
+// mirrored pairs (below), so a tile has 512 - 2 warm - S output positions.
 //
 // Band symmetry (Eq. (8)): for the filter over the extended line,
-// d^2(x+s, -s) = d^2(x, s), so only s = 1..S are filtered. The weight of the pair
+// d^2(x+s, -s) = d^2(x, s), so only s = 1..S are filtered. The weight w of the pair
 // (x, x+s) goes to pixel x with the difference f(x+s) - f(x) and to pixel x+s with
-// the opposite one; the latter is read back from a per-warp shared-memory row that
-// holds the weights of the current offset. Accumulation is centred as in the
-// running-sum passes: fhat = f(x) + A / (1 + Q), A = sum w (f(j) - f(x)), Q = sum w.
+// the opposite one: each lane pushes w and w (f(x+s) - f(x)) into two per-warp
+// shared-memory rows at position x+s (the index it read f(x+s) from), and after a
+// warp barrier every lane reads its own positions back. Accumulation is centred as in
+// the running-sum passes: fhat = f(x) + A / (1 + Q), A = sum w (f(j) - f(x)), Q = sum w.
 #include "snlm_host.h"
 #include "snlm_internal.h"
 
@@ -46,19 +47,21 @@ namespace {
 constexpr int kIirRun = 16;                      // positions per lane
 constexpr int kIirSpan = 32 * kIirRun;           // positions per warp window
 constexpr int kIirWarps = 8;                     // lines per CTA
-constexpr int kIirMaxHalo = 4;                   // halo lanes per side (beta <= 3.5)
-constexpr int kIirMaxRounds = 2;                 // scan rounds (2^rounds >= halo)
+constexpr int kIirMaxWarm = 64;                  // history samples a position needs (beta <= 3.5)
+constexpr int kIirMaxRounds = 2;                 // scan rounds (16 * 2^rounds >= warm)
 
 __host__ __device__ constexpr int iir_pad(int p) { return p + (p >> 4); }   // 32 lanes -> 32 banks
 
-constexpr int kIirLF = (iir_pad(kIirSpan + kMaxS) + 4) & ~3;   // line samples of a window
-constexpr int kIirLW = (iir_pad(kIirSpan) + 4) & ~3;           // weights of one offset
-constexpr int kIirPerWarp = kIirLF + kIirLW;
+// Floats of one per-warp row indexed by window position (padded), for a window of
+// 512 + S samples; a warp holds the samples, and for the NLM pass the pushed weights
+// and weighted differences as well.
+__host__ __device__ constexpr int iir_row(int S) { return (iir_pad(kIirSpan + S) + 4) & ~3; }
 
 struct IirArgs {
     Lines src;
     int n_lines, N, S;
-    int halo, rounds;            // halo lanes per side, scan rounds
+    int warm, rounds;            // history samples a position needs, scan rounds
+    int row;                     // iir_row(S)
     int T;                       // output positions per tile
     float a1, a2, a3;            // the recursion (its gain B is folded into c2 and scale)
     float phi[kIirRun][3];       // row 0 of A^(m+1): response of output m to the entering state
@@ -186,11 +189,12 @@ __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float
 template <bool DIST>
 __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirArgs a)
 {
-    __shared__ __align__(16) float smem[kIirWarps * kIirPerWarp];
+    extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *fs = smem + warp * kIirPerWarp;       // f(b0 + q), q < kIirSpan + S
-    float *ws = fs + kIirLF;                     // weights of the current offset
-    const int q0 = a.halo * kIirRun + a.S;       // window index of the tile's first output
+    float *fs = smem + warp * (DIST ? 1 : 3) * a.row;   // f(b0 + q), q < kIirSpan + S
+    float *pw = fs + a.row;                      // pushed weights of the current offset
+    float *pd = pw + a.row;                      // pushed weighted differences
+    const int q0 = a.warm + a.S;                 // window index of the tile's first output
     const int b0 = blockIdx.x * a.T - q0;        // line position of window index 0
     const int base = lane * kIirRun;
     const int nf = kIirSpan + a.S;
@@ -212,9 +216,10 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
         }
         for (int s = 1; s <= a.S; ++s) {
             float dl[kIirRun], y[kIirRun];
+            const int ib = base + s;
 #pragma unroll
             for (int m = 0; m < kIirRun; ++m)
-                dl[m] = fs[iir_pad(base + m + s)] - fo[m];
+                dl[m] = fs[iir_pad(ib + m)] - fo[m];
             iir_filter_run(dl, y, a, lane);
             if constexpr (DIST) {
                 const long long row = (long long)ln * a.N;
@@ -229,25 +234,24 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
                         a.dist[(row + x + s) * stride + a.S - s] = d;      // d^2(x+s, x)
                 }
             } else {
-                float wt[kIirRun];
 #pragma unroll
                 for (int m = 0; m < kIirRun; ++m) {
                     // the filter's response is non-negative, so a negative output is
                     // float rounding of a zero distance (weight 1)
-                    wt[m] = iir_ex2(fminf(a.c2 * y[m], 0.f));
-                    accA[m] = fmaf(wt[m], dl[m], accA[m]);
-                    accQ[m] += wt[m];
-                    ws[iir_pad(base + m)] = wt[m];
+                    const float wt = iir_ex2(fminf(a.c2 * y[m], 0.f));
+                    const float wd = wt * dl[m];
+                    accA[m] += wd;
+                    accQ[m] += wt;
+                    pw[iir_pad(ib + m)] = wt;            // the pair's share of pixel x + s
+                    pd[iir_pad(ib + m)] = wd;
                 }
                 __syncwarp();
-                // mirrored pairs: pixel q receives w(q - s, s) (f(q - s) - f(q)); window
-                // indices below 0 only occur in halo lanes, whose sums are discarded
+                // every position q >= s received the push of q - s; positions below s
+                // (stale values) lie before the tile's first output
 #pragma unroll
                 for (int m = 0; m < kIirRun; ++m) {
-                    const int q = max(base + m - s, 0);
-                    const float wm = ws[iir_pad(q)];
-                    accA[m] = fmaf(wm, fs[iir_pad(q)] - fo[m], accA[m]);
-                    accQ[m] += wm;
+                    accA[m] -= pd[iir_pad(base + m)];
+                    accQ[m] += pw[iir_pad(base + m)];
                 }
                 __syncwarp();
             }
@@ -312,29 +316,30 @@ int iir_plan(double beta, int S, IirArgs &a)
     if (!(beta >= kIirBetaMin && beta <= kIirBetaMax))
         return SNLM_ERR_ARG;
     const IirDesign d = iir_design(beta);
-    // samples after which the causal impulse response stays below 1e-10 of its peak
+    // samples after which the causal impulse response stays below 1e-9 of its peak:
+    // the truncated tail then moves an exponent d^2 / h^2 by at most about
+    // 1e-9 * 255^2 / sigma^2 (h^2 = sigma^2 beta sqrt(2 pi), the default rule)
     int warm = 0;
     {
         double w1 = 0, w2 = 0, w3 = 0, peak = 0;
         for (int n = 0; n < 4096; ++n) {
             const double v = (n == 0 ? d.B : 0.0) + d.a[0] * w1 + d.a[1] * w2 + d.a[2] * w3;
             peak = fmax(peak, fabs(v));
-            if (fabs(v) > 1e-10 * peak)
+            if (fabs(v) > 1e-9 * peak)
                 warm = n + 1;
             w3 = w2;
             w2 = w1;
             w1 = v;
         }
     }
-    a.halo = div_up(warm, kIirRun);
-    if (a.halo < 1)
-        a.halo = 1;
-    if (a.halo > kIirMaxHalo)
+    if (warm > kIirMaxWarm)
         return SNLM_ERR_ARG;
+    a.warm = warm;
     a.rounds = 0;
-    while ((1 << a.rounds) < a.halo)
+    while ((kIirRun << a.rounds) < warm)
         ++a.rounds;
-    a.T = kIirRun * (32 - 2 * a.halo) - S;
+    a.row = iir_row(S);
+    a.T = kIirSpan - 2 * warm - S;
     a.a1 = (float)d.a[0];
     a.a2 = (float)d.a[1];
     a.a3 = (float)d.a[2];
@@ -364,11 +369,18 @@ cudaError_t launch_iir(const IirArgs &a, bool dist, cudaStream_t st)
     const int tiles = div_up(a.N, a.T);
     const int groups = div_up(a.n_lines, kIirWarps);
     const dim3 grid((unsigned)tiles, (unsigned)(groups < 65535 ? groups : 65535));
-    if (dist)
-        iir_pass_kernel<true><<<grid, kIirWarps * 32, 0, st>>>(a);
-    else
-        iir_pass_kernel<false><<<grid, kIirWarps * 32, 0, st>>>(a);
-    return cudaGetLastError();
+    const int smem = kIirWarps * (dist ? 1 : 3) * a.row * (int)sizeof(float);   // <= 66 KB (S <= 128)
+    cudaError_t e;
+    if (dist) {
+        e = cudaFuncSetAttribute(iir_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            iir_pass_kernel<true><<<grid, kIirWarps * 32, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(iir_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            iir_pass_kernel<false><<<grid, kIirWarps * 32, smem, st>>>(a);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
