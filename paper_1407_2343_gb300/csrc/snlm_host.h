@@ -12,6 +12,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/snlm.h"
+#include "snlm_iir.h"
 #include "snlm_internal.h"
 
 namespace snlm {

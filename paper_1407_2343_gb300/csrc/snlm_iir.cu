@@ -36,6 +36,7 @@
 // warp barrier every lane reads its own positions back. Accumulation is centred as in
 // the running-sum passes: fhat = f(x) + A / (1 + Q), A = sum w (f(j) - f(x)), Q = sum w.
 #include "snlm_host.h"
+#include "snlm_iir.h"
 #include "snlm_internal.h"
 
 #include <cuda_fp16.h>

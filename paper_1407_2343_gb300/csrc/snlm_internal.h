@@ -28,14 +28,7 @@ enum DType { DT_U8 = 0, DT_F16 = 1, DT_F32 = 2 };
 //  SLIDE  running window sum (two updates per step) - exact for integer samples
 //  BLOCK  prefix/suffix sums inside blocks of 2K+1 samples (no long drift; float samples)
 //  FIR    the (2K+1)-tap weighted sum of the Gaussian profile
-//  IIR    the recursive Gaussian profile (snlm_iir.cu; its own kernels)
-enum DistMode { DIST_SLIDE = 0, DIST_BLOCK = 1, DIST_FIR = 2, DIST_IIR = 3 };
-
-// Widths of the recursive Gaussian profile the library accepts: Young and van
-// Vliet's rule for q holds from 0.5, and up to 3.5 (K = 7 at beta = K/2) the
-// filter's history fits the halo lanes of one warp window.
-constexpr double kIirBetaMin = 0.5;
-constexpr double kIirBetaMax = 3.5;
+enum DistMode { DIST_SLIDE = 0, DIST_BLOCK = 1, DIST_FIR = 2 };
 
 // Strided view of a set of 1-D signals: sample i of line l is at
 // ptr[l * line_step + i * elem_step] (elements of dtype).
@@ -185,15 +178,6 @@ cudaError_t launch_planned_tma(int K, const PassArgs &a, const TmaPass &t, int d
 constexpr int kTraceTma = 1 << 12;   // trace-kind flag: the launch used the TMA kernel
 
 template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);
-
-// Recursive Gaussian profile (snlm_iir.cu). iir_check_beta: SNLM_OK or SNLM_ERR_ARG.
-// run_iir_pass: the 1-D NLM of Eq. (4) over n_lines lines of `src` into dst (fhat,
-// or (fhat + blend) / 2 when blend is given). run_iir_dist: the distances
-// d^2(x, x+s), s in [-S, S], as (n_lines, N, 2S+1) float32.
-int iir_check_beta(double beta);
-cudaError_t run_iir_pass(const Lines &src, int n_lines, int N, int S, double h, double beta, float *dst,
-                         long long out_line_step, long long out_elem_step, const float *blend, cudaStream_t st);
-cudaError_t run_iir_dist(const Lines &src, int n_lines, int N, int S, double beta, float *out, cudaStream_t st);
 
 // scratch: 2 * kSolveScratchRecords * kPartials doubles
 constexpr int kSolveScratchRecords = 128;
