@@ -18,8 +18,8 @@
 // state, which gives the run's outputs w_loc and its end state v (the last three
 // outputs); the state entering lane r is sum_j A^(16 j) v_(r-1-j), formed by a
 // Kogge-Stone scan of warp shuffles with the 3x3 companion matrix A of the
-// recursion; each output then adds the response to that state, row 0 of A^(m+1)
-// times it. The anti-causal pass does the same from right to left.
+// recursion; the lane then runs its recursion again from that state. The
+// anti-causal pass does the same from right to left.
 //
 // The impulse response decays geometrically, so a position needs a bounded history:
 // the host sets `warm`, the number of samples after which the causal response stays
@@ -54,18 +54,16 @@ constexpr int kIirMaxRounds = 2;                 // scan rounds (16 * 2^rounds >
 __host__ __device__ constexpr int iir_pad(int p) { return p + (p >> 4); }   // 32 lanes -> 32 banks
 
 // Floats of one per-warp row indexed by window position (padded), for a window of
-// 512 + S samples; a warp holds the samples, and for the NLM pass the pushed weights
-// and weighted differences as well.
-__host__ __device__ constexpr int iir_row(int S) { return (iir_pad(kIirSpan + S) + 4) & ~3; }
+// 512 + S <= 640 samples; a warp holds the samples, and for the NLM pass the pushed
+// weights and weighted differences as well, at fixed offsets from the samples.
+constexpr int kIirRow = (iir_pad(kIirSpan + kMaxS) + 4) & ~3;
 
 struct IirArgs {
     Lines src;
     int n_lines, N, S;
     int warm, rounds;            // history samples a position needs, scan rounds
-    int row;                     // iir_row(S)
     int T;                       // output positions per tile
     float a1, a2, a3;            // the recursion (its gain B is folded into c2 and scale)
-    float phi[kIirRun][3];       // row 0 of A^(m+1): response of output m to the entering state
     float P[kIirMaxRounds][9];   // A^(16 * 2^d), row-major
     float c2;                    // -log2(e) beta sqrt(2 pi) B^2 / h^2: w = 2^(c2 * y)
     float scale;                 // beta sqrt(2 pi) B^2: distance = scale * y
@@ -87,15 +85,51 @@ __device__ __forceinline__ int iir_reflect(int x, int n)
     return y < n ? y : p - 1 - y;
 }
 
-// Element offsets fit in 31 bits (checked by the host before any launch).
-__device__ __forceinline__ float iir_load(const Lines &v, int line, int i)
+// A warp's window into its shared-memory row: fs[pad(q)] = sample at line position
+// b0 + q (through the extension), q < nf, lane q of every 32. The loads go out in
+// batches of five, each issued before its first value is stored (five slots at a time
+// keep the pass kernels within their register budget). Element offsets fit in 31 bits
+// (checked by the host before any launch).
+constexpr int kIirLoadSlots = (kIirSpan + kMaxS + 31) / 32;
+
+template <typename T>
+__device__ __forceinline__ void iir_gather_t(float *fs, const T *p, unsigned base, int es, int N,
+                                             int b0, int lane, int nf)
 {
-    const unsigned off = (unsigned)(line * (int)v.line_step + i * (int)v.elem_step);
-    if (v.dtype == DT_U8)
-        return (float)__ldg(static_cast<const unsigned char *>(v.ptr) + off);
-    if (v.dtype == DT_F16)
-        return __half2float(__ldg(static_cast<const __half *>(v.ptr) + off));
-    return __ldg(static_cast<const float *>(v.ptr) + off);
+#pragma unroll 1
+    for (int j0 = 0; j0 < kIirLoadSlots; j0 += 5) {
+        float v[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int q = lane + 32 * (j0 + j);
+            if (q < nf) {
+                const T t = __ldg(p + base + (unsigned)(iir_reflect(b0 + q, N) * es));
+                if constexpr (sizeof(T) == 2)
+                    v[j] = __half2float(t);
+                else
+                    v[j] = (float)t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int q = lane + 32 * (j0 + j);
+            if (q < nf)
+                fs[iir_pad(q)] = v[j];
+        }
+    }
+}
+
+__device__ __forceinline__ void iir_gather(float *fs, const Lines &src, int ln, int N, int b0,
+                                           int lane, int nf)
+{
+    const unsigned base = (unsigned)(ln * (int)src.line_step);
+    const int es = (int)src.elem_step;
+    if (src.dtype == DT_U8)
+        iir_gather_t(fs, static_cast<const unsigned char *>(src.ptr), base, es, N, b0, lane, nf);
+    else if (src.dtype == DT_F16)
+        iir_gather_t(fs, static_cast<const __half *>(src.ptr), base, es, N, b0, lane, nf);
+    else
+        iir_gather_t(fs, static_cast<const float *>(src.ptr), base, es, N, b0, lane, nf);
 }
 
 __device__ __forceinline__ float iir_ex2(float x)
@@ -142,46 +176,62 @@ __device__ __forceinline__ void scan_state(float v0, float v1, float v2, const I
 // each pass is taken out of the recursions (u = w / B runs u(x) = F(x) + a1 u(x-1) +
 // a2 u(x-2) + a3 u(x-3), and y / B^2 the same recursion on u) and folded into the
 // host's distance scale and exponent factor, which saves one multiply per pass.
+// Each pass runs twice over the lane's run: from rest, for the run's end state that
+// the scan combines, then from the state entering the run. (Adding the entering
+// state's response afterwards takes as many operations but a table of 48 responses
+// that costs the kernel its registers.)
 __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float (&y)[kIirRun], const IirArgs &a,
                                                int lane)
 {
     float w[kIirRun];
-    {
-        float w1 = 0.f, w2 = 0.f, w3 = 0.f;
+    float w1 = 0.f, w2 = 0.f, w3 = 0.f;
 #pragma unroll
-        for (int m = 0; m < kIirRun; ++m) {
-            float v = fmaf(dl[m], dl[m], a.a3 * w3);
-            v = fmaf(a.a2, w2, v);
-            v = fmaf(a.a1, w1, v);
-            w[m] = v;
-            w3 = w2;
-            w2 = w1;
-            w1 = v;
-        }
+    for (int m = 0; m < kIirRun; ++m) {          // from rest: the run's end state
+        float v = fmaf(dl[m], dl[m], a.a3 * w3);
+        v = fmaf(a.a2, w2, v);
+        v = fmaf(a.a1, w1, v);
+        w3 = w2;
+        w2 = w1;
+        w1 = v;
     }
     float e0, e1, e2;
-    scan_state<true>(w[kIirRun - 1], w[kIirRun - 2], w[kIirRun - 3], a, lane, e0, e1, e2);
+    scan_state<true>(w1, w2, w3, a, lane, e0, e1, e2);
+    w1 = e0;
+    w2 = e1;
+    w3 = e2;
 #pragma unroll
-    for (int m = 0; m < kIirRun; ++m)
-        w[m] = fmaf(a.phi[m][0], e0, fmaf(a.phi[m][1], e1, fmaf(a.phi[m][2], e2, w[m])));
-    {
-        float y1 = 0.f, y2 = 0.f, y3 = 0.f;
-#pragma unroll
-        for (int m = kIirRun - 1; m >= 0; --m) {
-            float v = fmaf(a.a3, y3, w[m]);
-            v = fmaf(a.a2, y2, v);
-            v = fmaf(a.a1, y1, v);
-            y[m] = v;
-            y3 = y2;
-            y2 = y1;
-            y1 = v;
-        }
+    for (int m = 0; m < kIirRun; ++m) {          // from the state entering the run
+        float v = fmaf(dl[m], dl[m], a.a3 * w3);
+        v = fmaf(a.a2, w2, v);
+        v = fmaf(a.a1, w1, v);
+        w[m] = v;
+        w3 = w2;
+        w2 = w1;
+        w1 = v;
     }
-    scan_state<false>(y[0], y[1], y[2], a, lane, e0, e1, e2);
+    float y1 = 0.f, y2 = 0.f, y3 = 0.f;
 #pragma unroll
-    for (int m = 0; m < kIirRun; ++m) {
-        const int k = kIirRun - 1 - m;
-        y[m] = fmaf(a.phi[k][0], e0, fmaf(a.phi[k][1], e1, fmaf(a.phi[k][2], e2, y[m])));
+    for (int m = kIirRun - 1; m >= 0; --m) {     // anti-causal, from rest
+        float v = fmaf(a.a3, y3, w[m]);
+        v = fmaf(a.a2, y2, v);
+        v = fmaf(a.a1, y1, v);
+        y3 = y2;
+        y2 = y1;
+        y1 = v;
+    }
+    scan_state<false>(y1, y2, y3, a, lane, e0, e1, e2);
+    y1 = e0;
+    y2 = e1;
+    y3 = e2;
+#pragma unroll
+    for (int m = kIirRun - 1; m >= 0; --m) {     // and from the state entering from the right
+        float v = fmaf(a.a3, y3, w[m]);
+        v = fmaf(a.a2, y2, v);
+        v = fmaf(a.a1, y1, v);
+        y[m] = v;
+        y3 = y2;
+        y2 = y1;
+        y1 = v;
     }
 }
 
@@ -192,9 +242,9 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
 {
     extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *fs = smem + warp * (DIST ? 1 : 3) * a.row;   // f(b0 + q), q < kIirSpan + S
-    float *pw = fs + a.row;                      // pushed weights of the current offset
-    float *pd = pw + a.row;                      // pushed weighted differences
+    float *fs = smem + warp * (DIST ? 1 : 3) * kIirRow;  // f(b0 + q), q < kIirSpan + S
+    float *pw = fs + kIirRow;                    // pushed weights of the current offset
+    float *pd = pw + kIirRow;                    // pushed weighted differences
     const int q0 = a.warm + a.S;                 // window index of the tile's first output
     const int b0 = blockIdx.x * a.T - q0;        // line position of window index 0
     const int base = lane * kIirRun;
@@ -205,8 +255,7 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
         if (ln >= a.n_lines)
             continue;                            // warps work independently (no CTA barrier)
         __syncwarp();
-        for (int q = lane; q < nf; q += 32)
-            fs[iir_pad(q)] = iir_load(a.src, ln, iir_reflect(b0 + q, a.N));
+        iir_gather(fs, a.src, ln, a.N, b0, lane, nf);
         __syncwarp();
         float fo[kIirRun], accA[kIirRun], accQ[kIirRun];
 #pragma unroll
@@ -247,8 +296,9 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
                     pd[iir_pad(ib + m)] = wd;
                 }
                 __syncwarp();
-                // every position q >= s received the push of q - s; positions below s
-                // (stale values) lie before the tile's first output
+                // every position q >= s received the push of q - s, whose difference
+                // has the opposite sign; positions below s (stale values) lie before the
+                // tile's first output
 #pragma unroll
                 for (int m = 0; m < kIirRun; ++m) {
                     accA[m] -= pd[iir_pad(base + m)];
@@ -339,23 +389,16 @@ int iir_plan(double beta, int S, IirArgs &a)
     a.rounds = 0;
     while ((kIirRun << a.rounds) < warm)
         ++a.rounds;
-    a.row = iir_row(S);
     a.T = kIirSpan - 2 * warm - S;
     a.a1 = (float)d.a[0];
     a.a2 = (float)d.a[1];
     a.a3 = (float)d.a[2];
     // companion matrix of the recursion: state (w(x), w(x-1), w(x-2))
     const double A[9] = {d.a[0], d.a[1], d.a[2], 1, 0, 0, 0, 1, 0};
-    double Pm[9];
-    memcpy(Pm, A, sizeof(Pm));
-    for (int m = 0; m < kIirRun; ++m) {          // Pm = A^(m+1)
-        for (int c = 0; c < 3; ++c)
-            a.phi[m][c] = (float)Pm[c];
-        if (m + 1 < kIirRun)
-            mat3_mul(Pm, A, Pm);
-    }
     double R[9];
-    memcpy(R, Pm, sizeof(R));                    // A^16: the transfer over one lane's run
+    memcpy(R, A, sizeof(R));
+    for (int m = 1; m < kIirRun; ++m)            // A^16: the transfer over one lane's run
+        mat3_mul(R, A, R);
     for (int r = 0; r < kIirMaxRounds; ++r) {    // A^(16 * 2^r)
         for (int c = 0; c < 9; ++c)
             a.P[r][c] = (float)R[c];
@@ -370,7 +413,7 @@ cudaError_t launch_iir(const IirArgs &a, bool dist, cudaStream_t st)
     const int tiles = div_up(a.N, a.T);
     const int groups = div_up(a.n_lines, kIirWarps);
     const dim3 grid((unsigned)tiles, (unsigned)(groups < 65535 ? groups : 65535));
-    const int smem = kIirWarps * (dist ? 1 : 3) * a.row * (int)sizeof(float);   // <= 66 KB (S <= 128)
+    const int smem = kIirWarps * (dist ? 1 : 3) * kIirRow * (int)sizeof(float);   // 66 KB (pass), 22 KB
     cudaError_t e;
     if (dist) {
         e = cudaFuncSetAttribute(iir_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
