@@ -180,6 +180,30 @@ def test_unsupported_and_invalid_requests(dev, api):
     assert e.value.status == api.ERR_UNSUPPORTED
 
 
+def test_other_entry_points_run_the_recursive_profile(dev, api, orc):
+    # the host-buffer, pipelined, allocation-free and post-filtered entry points give
+    # the device path's result (they share its passes), and the device path the oracle's
+    import torch
+
+    sigma, S, K, beta = 25.0, 8, 3, 1.5
+    img = synth.noisy_image(120, 90, sigma, seed=12, dtype="u8")
+    h = orc.default_h(sigma, K, "gauss_iir", beta)
+    dev_out = np_of(api.snlm_denoise(to_dev(img, dev), S, K, h, "gauss_iir", "CR", 0.0, beta))
+    ref, _ = orc.snlm(img.astype(np.float64), S, K, h, "gauss_iir", beta, order="CR")
+    assert np.abs(dev_out - ref).max() <= TOL
+    host = api.snlm_denoise_host(img, S, K, h, "gauss_iir", "CR", 0.0, beta)
+    np.testing.assert_array_equal(np.asarray(host), dev_out)
+    many = api.snlm_denoise_host_many([img, img], S, K, h, "gauss_iir", "CR", 0.0, beta)
+    for o in many:
+        np.testing.assert_array_equal(np.asarray(o), dev_out)
+    out = torch.empty((120, 90), dtype=torch.float32, device=dev)
+    api.snlm_denoise_noalloc(to_dev(img, dev), S, K, h, "gauss_iir", "CR", 0.0, beta, out=out)
+    np.testing.assert_array_equal(np_of(out), dev_out)
+    ss, sr = api.snlm_bf_params(sigma)
+    bf = np_of(api.snlm_denoise_bf(to_dev(img, dev), S, K, h, "gauss_iir", "CR", sigma, beta))
+    np.testing.assert_array_equal(bf, np_of(api.snlm_bilateral(to_dev(dev_out, dev), ss, sr)))
+
+
 def test_trace_names_the_recursive_passes(dev, api):
     img = to_dev(synth.noisy_image(64, 64, 20.0, seed=1, dtype="u8"), dev)
     api.snlm_trace_enable(True)
