@@ -48,7 +48,7 @@ namespace {
 constexpr int kIirRun = 16;                      // positions per lane
 constexpr int kIirSpan = 32 * kIirRun;           // positions per warp window
 constexpr int kIirWarps = 8;                     // lines per CTA
-constexpr int kIirMaxWarm = 64;                  // history samples a position needs (beta <= 3.5)
+constexpr int kIirMaxWarm = 64;                  // history a position may need (58 at beta = 3.5)
 constexpr int kIirMaxRounds = 2;                 // scan rounds (16 * 2^rounds >= warm)
 
 __host__ __device__ constexpr int iir_pad(int p) { return p + (p >> 4); }   // 32 lanes -> 32 banks

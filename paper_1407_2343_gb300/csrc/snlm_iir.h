@@ -13,7 +13,7 @@ constexpr int DIST_IIR = 3;
 
 // Widths of the recursive Gaussian profile the library accepts: Young and van
 // Vliet's rule for q holds from 0.5, and up to 3.5 (K = 7 at beta = K/2) the
-// filter's history (64 samples) fits the scan of one warp window.
+// filter's history (58 samples at 3.5) fits the scan of one warp window (at most 64).
 constexpr double kIirBetaMin = 0.5;
 constexpr double kIirBetaMax = 3.5;
 

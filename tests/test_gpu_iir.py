@@ -1,18 +1,17 @@
 """Parity of the recursive Gaussian profile (SNLM_GAUSS_IIR) with the FP64 oracle.
 
 The CUDA path runs the Young-van Vliet recursion in float32 as a scan over the
-lanes of a warp (each lane recurs over 16 positions from rest; the states are
-combined across lanes by shuffles) and truncates the filter's history where its
-causal response falls below 1e-10 of its peak; the oracle recurs sequentially in
-FP64 from rest far outside the line. Tolerances from that arithmetic:
+lanes of a warp (each lane recurs over its 16 positions from rest, the end states
+are combined across lanes by shuffles, and each lane recurs again from the state
+entering its run) and truncates the filter's history where its causal response
+falls below 1e-9 of its peak; the oracle recurs sequentially in FP64 from rest far
+outside the line. Tolerances from that arithmetic:
   distances   |gpu - oracle| <= 1e-5 * (largest distance of the line) + 1e-5 * oracle:
               float32 rounding of the recursion grows with the state it carries
               (a few 1e-7 of the line's largest value per pass, amplified by
               1/B of the recursion: about 15 at beta = 3.5);
   pixels      1e-4 max-abs on the [0, 255] scale, as for every float32 output.
 """
-import math
-
 import numpy as np
 import pytest
 
