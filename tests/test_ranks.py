@@ -81,3 +81,63 @@ def test_reference_arm_runs_on_rank_zero_only():
                        text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+SURE_BAND_CODE = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+import torch.distributed as dist
+dist.init_process_group("gloo", init_method="env://")
+import oracle
+from paper_1407_2343_gb300 import shard, synth
+rank, world = dist.get_rank(), dist.get_world_size()
+sigma, S, K = 20.0, 5, 2
+img = synth.noisy_image(61, 44, sigma, seed=3, dtype="f32").astype(np.float64)
+h = oracle.default_h(sigma, K)
+r0, r1, h0, h1 = shard.band_plan(img.shape[0], world, shard.reach(S, K))[rank]
+p = oracle.snlm_parts(img[h0:h1], S, K, h)
+sl = slice(r0 - h0, r1 - h0)
+f, frc, fcr = img[r0:r1], p["frc"][sl], p["fcr"][sl]
+sums = torch.tensor([(frc * frc).sum(), (frc * fcr).sum(), (fcr * fcr).sum(), (f * frc).sum(), (f * fcr).sum(),
+                     p["d1"][sl].sum(), p["d2"][sl].sum()], dtype=torch.float64)
+dist.all_reduce(sums)                          # the one exchange of a banded SURE run
+a11, a12, a22, bf1, bf2, sd1, sd2 = sums.tolist()
+b1, b2 = bf1 - sigma ** 2 * sd1, bf2 - sigma ** 2 * sd2
+det = a11 * a22 - a12 * a12
+theta = [(a22 * b1 - a12 * b2) / det, (a11 * b2 - a12 * b1) / det]
+dist.destroy_process_group()
+print(json.dumps({{"rank": rank, "theta": theta, "sums": sums.tolist()}}), flush=True)
+"""
+
+
+def test_banded_sure_sums_all_reduce_over_two_gloo_ranks(orc):
+    # the exchange step of a single image split into row bands: each rank forms the
+    # seven sums of Eqs. (19) and (25) over its own rows (from a crop widened by the
+    # passes' reach), one all-reduce adds them, and every rank solves the 2x2 system:
+    # the result is the unsharded image's (oracle arithmetic on both sides)
+    port = _free_port()
+    code = SURE_BAND_CODE.format(root=ROOT)
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=_env(r, 2, port), stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for r in range(2)]
+    outs = []
+    for p in procs:
+        try:
+            o, e = p.communicate(timeout=180)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            pytest.fail("a gloo rank did not finish")
+        assert p.returncode == 0, e
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    import numpy as np
+
+    from paper_1407_2343_gb300 import synth
+
+    sigma, S, K = 20.0, 5, 2
+    img = synth.noisy_image(61, 44, sigma, seed=3, dtype="f32").astype(np.float64)
+    _, info = orc.snlm(img, S, K, orc.default_h(sigma, K), order="SURE", sigma=sigma)
+    want = [info["A11"], info["A12"], info["A22"], info["sum_f_frc"], info["sum_f_fcr"], info["sum_d1"], info["sum_d2"]]
+    for o in outs:
+        assert o["sums"] == pytest.approx(want, rel=1e-12)
+        assert o["theta"] == pytest.approx([info["theta1"], info["theta2"]], rel=1e-9)
