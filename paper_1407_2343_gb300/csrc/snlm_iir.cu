@@ -15,8 +15,8 @@
 // b0 + 16 r .. b0 + 16 r + 15 of a 512-position window. A recursion along the
 // window is spread over the lanes as a scan of affine maps (the parallel evaluation
 // of a linear recurrence): each lane runs the recursion over its own run from a zero
-// state, which gives the run's outputs w_loc and its end state v (the last three
-// outputs); the state entering lane r is sum_j A^(16 j) v_(r-1-j), formed by a
+// state, which gives the run's end state v (its last three outputs); the state
+// entering lane r is sum_j A^(16 j) v_(r-1-j), formed by a
 // Kogge-Stone scan of warp shuffles with the 3x3 companion matrix A of the
 // recursion; the lane then runs its recursion again from that state. The
 // anti-causal pass does the same from right to left.
