@@ -555,3 +555,34 @@ def test_3d_extension_constant_volume_and_average(orc):
     vol = np.random.default_rng(23).uniform(0, 255, (4, 5, 6))
     avg = orc.snlm_3d(vol, 2, 1, 50.0, order="AVG6")
     assert avg.min() >= vol.min() - 1e-9 and avg.max() <= vol.max() + 1e-9
+
+
+# ---------------------------------------------------------------- closed form: a two-level step
+
+def _step_nlm(N, c, a, b, S, K, h, g):
+    # f = a left of c, b from c on; away from the ends the symmetric extension keeps
+    # the step, and the patches centred at x and x+s differ exactly at the taps k
+    # with x + k < c <= x + s + k (s > 0; mirrored for s < 0), each by (b - a)^2
+    out = np.empty(N)
+    for x in range(N):
+        num = den = 0.0
+        for s in range(-S, S + 1):
+            lo, hi = (c - x - s, c - x - 1) if s > 0 else (c - x, c - x - s - 1)
+            taps = [k for k in range(max(lo, -K), min(hi, K) + 1)]
+            d2 = (b - a) ** 2 * sum(g[k + K] for k in taps) if s != 0 else 0.0
+            w = math.exp(-d2 / (h * h))
+            num += w * (a if x + s < c else b)
+            den += w
+        out[x] = num / den
+    return out
+
+
+@pytest.mark.parametrize("prof,K,beta", [("box", 3, None), ("gauss", 4, 1.5), ("box", 0, None)])
+def test_nlm_of_a_step_matches_its_closed_form(orc, prof, K, beta):
+    N, c, a, b, S, h = 60, 27, 10.0, 40.0, 6, 35.0
+    x = np.where(np.arange(N) < c, a, b)
+    g = orc.profile(K, prof, beta) if prof == "gauss" else np.ones(2 * K + 1)
+    want = _step_nlm(N, c, a, b, S, K, h, g)
+    got = orc.nlm_1d(x[None], S, K, h, prof, beta)[0]
+    inner = slice(S + K, N - S - K)            # the extension keeps the step there
+    np.testing.assert_allclose(got[inner], want[inner], rtol=1e-13, atol=1e-12)

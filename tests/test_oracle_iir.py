@@ -223,3 +223,24 @@ def test_rejections(orc):
         orc.nlm_1d(x, 2, 0, 1.0, "gauss_iir", 1.0, with_delta=True)   # no divergence for this profile
     with pytest.raises(ValueError):
         orc.snlm(np.zeros((4, 4)), 2, 2, 1.0, "gauss_iir", 1.0, order="SURE", sigma=1.0)
+
+
+def test_nlm_of_a_step_matches_its_closed_form(orc):
+    # a two-level step: the lifted squares of offset s are (b - a)^2 on the s samples
+    # whose patch pairs straddle the step and zero elsewhere, so the distance is
+    # beta sqrt(2 pi) (b - a)^2 times the impulse response summed over those taps
+    beta, N, c, a, b, S, h = 2.0, 400, 190, 10.0, 40.0, 6, 60.0
+    hr, k = _impulse(orc, beta)
+    L = len(k) // 2
+    x = np.where(np.arange(N) < c, a, b)
+    got = orc.nlm_1d(x[None], S, 0, h, "gauss_iir", beta)[0]
+    scale = beta * math.sqrt(2 * math.pi)
+    for i in range(150, 230):                       # far from the line's ends
+        num = den = 0.0
+        for s in range(-S, S + 1):
+            lo, hi = (c - i - s, c - i - 1) if s > 0 else (c - i, c - i - s - 1)
+            d2 = scale * (b - a) ** 2 * sum(hr[L + kk] for kk in range(lo, hi + 1)) if s != 0 else 0.0
+            w = math.exp(-d2 / (h * h))
+            num += w * (a if i + s < c else b)
+            den += w
+        assert got[i] == pytest.approx(num / den, rel=1e-12, abs=1e-10)
