@@ -586,3 +586,18 @@ def test_nlm_of_a_step_matches_its_closed_form(orc, prof, K, beta):
     got = orc.nlm_1d(x[None], S, K, h, prof, beta)[0]
     inner = slice(S + K, N - S - K)            # the extension keeps the step there
     np.testing.assert_allclose(got[inner], want[inner], rtol=1e-13, atol=1e-12)
+
+
+def test_alg4_on_an_image_constant_along_columns_is_the_1d_closed_form(orc):
+    # f(y, x) = step(x): every column is constant, so a column pass changes nothing
+    # (all its patch distances are 0 and the window mean of equal samples is the
+    # sample), and both orders of Alg. 4 reduce to the 1-D NLM of the step in each row
+    N, c, a, b, S, K, h = 48, 21, 10.0, 40.0, 5, 2, 30.0
+    row = np.where(np.arange(N) < c, a, b)
+    img = np.tile(row, (17, 1))
+    want = _step_nlm(N, c, a, b, S, K, h, np.ones(2 * K + 1))
+    inner = slice(S + K, N - S - K)
+    for order in ("RC", "CR", "AVG"):
+        out, _ = orc.snlm(img, S, K, h, "box", order=order)
+        np.testing.assert_allclose(out[:, inner], np.broadcast_to(want[inner], out[:, inner].shape),
+                                   rtol=1e-13, atol=1e-12)
