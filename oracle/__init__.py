@@ -225,15 +225,13 @@ def snlm(img, S: int, K: int, h: float, prof="box", beta: float | None = None, o
 
 
 def snlm_parts(img, S: int, K: int, h: float, prof="box", beta: float | None = None, nthreads: int = 0):
-    """The intermediate results of Alg. 4: dict with fr, frc, fc, fcr, d1, d2 (no
-    d1, d2 for the recursive Gaussian profile, which has no divergence here)."""
+    """The intermediate results of Alg. 4: dict with fr, frc, fc, fcr, d1, d2."""
     x = _f64(img)
     H, W = x.shape
-    keys = ("fr", "frc", "fc", "fcr") if _profile_id(prof) == GAUSS_IIR else ("fr", "frc", "fc", "fcr", "d1", "d2")
-    parts = {k: np.empty_like(x) for k in keys}
+    parts = {k: np.empty_like(x) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")}
     rc = _load().orc_snlm_parts(_ptr(x), H, W, S, K, float(h), _profile_id(prof),
                                 float(beta if beta is not None else default_beta(K)),
-                                *[_ptr(parts.get(k)) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")],
+                                *[_ptr(parts[k]) for k in ("fr", "frc", "fc", "fcr", "d1", "d2")],
                                 _nt(nthreads))
     if rc != 0:
         raise ValueError(f"oracle snlm_parts rejected its arguments (rc={rc})")

@@ -32,7 +32,9 @@
  *    output times beta*sqrt(2 pi), the integral of g_beta. Its support is
  *    infinite: both passes start from a zero state far enough outside [0, N)
  *    (iir_margin) that the truncated tail is below double rounding.
- *    The divergence of Eq. (24) is not defined for this profile here.
+ *    Its divergence is Eq. (24) with the profile's own centre weight g(0) (not 1)
+ *    and the patch term over every offset of the window, weighted by the profile
+ *    at that lag (its support is unbounded).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (no fast-math).
  */
@@ -224,6 +226,30 @@ static int iir_dist_table(const double *f, int64_t n, int64_t stride, int S, dou
     return 0;
 }
 
+/* Weights of the recursive profile at the lags s in [-S, S]: geff[s + S] =
+ * beta sqrt(2 pi) times the two-pass impulse response at lag s, i.e. the weight of
+ * the lifted square at i + s in d^2(i, .). Returns -1 on a bad beta, -3 when out of
+ * memory. */
+static int iir_lag_weights(double beta, int S, double *geff)
+{
+    const int64_t M = orc_iir_margin(beta);
+    if (M < 0)
+        return -1;
+    const int64_t L = M + S, n = 2 * L + 1;
+    double *x = (double *)calloc((size_t)n, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!x || !y) {
+        free(x); free(y);
+        return -3;
+    }
+    x[L] = 1.0;
+    orc_iir_filter(x, n, beta, y);
+    for (int s = -S; s <= S; ++s)
+        geff[s + S] = iir_scale(beta) * y[L + s];
+    free(x); free(y);
+    return 0;
+}
+
 /* Patch distances of n_lines signals of length N (row-major, line after line):
  * out[(line*N + i)*(2S+1) + (s+S)] = d^2(i, i+s) of Eq. (3), s in [-S, S]. */
 int orc_patch_dist_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, int profile,
@@ -265,14 +291,19 @@ int orc_patch_dist_1d(const double *x, int64_t n_lines, int64_t N, int S, int K,
  * with d^2 from Eq. (3). `din` may alias `dout`; either may be NULL together. */
 static void nlm_line(const double *f, int64_t N, int64_t stride, const double *din, double *fhat,
                      double *dout, int64_t ostride, int S, int K, double h, const double *g,
-                     const double *dtab, double *fe /* scratch, N + 2(S+K) */)
+                     const double *dtab, const double *geff, double *fe /* scratch, N + 2(S+K) */)
 {
-    /* dtab (recursive Gaussian profile only): the distances of iir_dist_table,
-     * used in place of the (2K+1)-tap sums; dout is NULL then. */
+    /* dtab, geff (recursive Gaussian profile only): the distances of iir_dist_table,
+     * used in place of the (2K+1)-tap sums, and the profile's weight at each lag
+     * s in [-S, S] (geff[s + S]), which Eq. (24) needs in place of g. */
     const int64_t R = (int64_t)S + K;
     extend_line(f, N, stride, R, fe);
     const double h2 = h * h;
-    const int KT = K < S ? K : S; /* patch-overlap offsets that lie in the window */
+    /* patch-overlap offsets that lie in the window: |s| <= K for the (2K+1)-tap
+     * profiles, the whole window for the recursive one (its support is unbounded) */
+    const int KT = geff ? S : (K < S ? K : S);
+    /* weight of the centre tap: g(0) = 1 for the tap profiles */
+    const double g0 = geff ? geff[S] : 1.0;
     for (int64_t i = 0; i < N; ++i) {
         const int64_t ci = R + i;
         double W = 0.0, P1 = 0.0, P2 = 0.0;
@@ -287,14 +318,18 @@ static void nlm_line(const double *f, int64_t N, int64_t stride, const double *d
         const double fh = P1 / W;
         fhat[i * ostride] = fh;
         if (dout) {
-            /* Last term of Eq. (24): sum over |j - i| <= K of
-             * w_ij g(i-j) (f(j) - fhat(i)) (f(2i-j) - f(i)). */
+            /* Last term of Eq. (24): sum over the offsets where the patches of i and j
+             * share the sample f(i) of w_ij g(i-j) (f(j) - fhat(i)) (f(2i-j) - f(i)). */
             double T = 0.0;
             for (int s = -KT; s <= KT; ++s) {
-                double w = exp(-patch_dist2(fe, ci, ci + s, K, g) / h2);
-                T += w * g[-s + K] * (fe[ci + s] - fh) * (fe[ci - s] - fe[ci]);
+                const double d2 = dtab ? dtab[i * (2 * S + 1) + (s + S)] : patch_dist2(fe, ci, ci + s, K, g);
+                const double gs = geff ? geff[-s + S] : g[-s + K];
+                T += exp(-d2 / h2) * gs * (fe[ci + s] - fh) * (fe[ci - s] - fe[ci]);
             }
-            double div = 2.0 / (h2 * W) * P2 + 1.0 / W - 2.0 / h2 * fh * fh + 2.0 / (W * h2) * T;
+            /* Eq. (24); its first terms carry the centre weight g(0), which is 1 for the
+             * tap profiles (the general form of d d^2_ij / d f(i) = 2 g(0) (f(i) - f(j))
+             * - 2 g(i-j) (f(2i-j) - f(i))) */
+            double div = 2.0 * g0 / (h2 * W) * P2 + 1.0 / W - 2.0 * g0 / h2 * fh * fh + 2.0 / (W * h2) * T;
             double d0 = din ? din[i * ostride] : 1.0;
             dout[i * ostride] = d0 * div;
         }
@@ -311,10 +346,13 @@ int orc_nlm_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, double
     const int iir = profile == ORC_GAUSS_IIR;
     if (iir && orc_iir_margin(beta) < 0)
         return -1;
-    if (iir && delta_out)
-        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
+    double *geff = iir ? (double *)malloc(sizeof(double) * (size_t)(2 * S + 1)) : NULL;
+    if (iir && (!geff || iir_lag_weights(beta, S, geff) != 0)) {
+        free(geff);
+        return -3;
+    }
     const int64_t L = N + 2 * ((int64_t)S + K);
     int rc = 0;
 #pragma omp parallel for schedule(static) num_threads(nthreads) reduction(min : rc)
@@ -326,11 +364,12 @@ int orc_nlm_1d(const double *x, int64_t n_lines, int64_t N, int S, int K, double
             r = iir_dist_table(x + ln * N, N, 1, S, beta, dtab);
         if (r == 0)
             nlm_line(x + ln * N, N, 1, delta_in ? delta_in + ln * N : NULL, fhat + ln * N,
-                     delta_out ? delta_out + ln * N : NULL, 1, S, K, h, g, dtab, fe);
+                     delta_out ? delta_out + ln * N : NULL, 1, S, K, h, g, dtab, geff, fe);
         rc = r < rc ? r : rc;
         free(fe);
         free(dtab);
     }
+    free(geff);
     return rc;
 }
 
@@ -345,6 +384,11 @@ static int sweep(const double *src, double *dst, double *delta, int64_t H, int64
     const int64_t elem_step = axis == 0 ? 1 : W;
     const int64_t L = N + 2 * ((int64_t)S + K);
     const int iir = profile == ORC_GAUSS_IIR;
+    double *geff = iir ? (double *)malloc(sizeof(double) * (size_t)(2 * S + 1)) : NULL;
+    if (iir && (!geff || iir_lag_weights(beta, S, geff) != 0)) {
+        free(geff);
+        return -3;
+    }
     int rc = 0;
 #pragma omp parallel for schedule(static) num_threads(nthreads) reduction(min : rc)
     for (int64_t ln = 0; ln < n_lines; ++ln) {
@@ -356,11 +400,12 @@ static int sweep(const double *src, double *dst, double *delta, int64_t H, int64
         if (r == 0)
             nlm_line(src + ln * line_step, N, elem_step, delta ? delta + ln * line_step : NULL,
                      dst + ln * line_step, delta ? delta + ln * line_step : NULL, elem_step, S, K, h, g,
-                     dtab, fe);
+                     dtab, geff, fe);
         rc = r < rc ? r : rc;
         free(fe);
         free(dtab);
     }
+    free(geff);
     return rc;
 }
 
@@ -419,8 +464,6 @@ int orc_snlm(const double *img, int64_t H, int64_t W, int S, int K, double h, in
         return -1;
     if (profile == ORC_GAUSS_IIR && orc_iir_margin(beta) < 0)
         return -1;
-    if (profile == ORC_GAUSS_IIR && order == ORC_SURE)
-        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
     const int64_t n = H * W;
@@ -501,11 +544,8 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
 {
     if (H < 1 || W < 1 || S < 0 || K < 0 || K > 64 || !(h > 0.0))
         return -1;
-    const int iir = profile == ORC_GAUSS_IIR;
-    if (iir && orc_iir_margin(beta) < 0)
+    if (profile == ORC_GAUSS_IIR && orc_iir_margin(beta) < 0)
         return -1;
-    if (iir && (d1 || d2))
-        return -2;
     double g[2 * 64 + 1];
     orc_profile(K, profile, beta, g);
     const int64_t n = H * W;
@@ -519,15 +559,14 @@ int orc_snlm_parts(const double *img, int64_t H, int64_t W, int S, int K, double
     }
     for (int64_t p = 0; p < n; ++p)
         da[p] = db[p] = 1.0;
-    double *pa = iir ? NULL : da, *pb = iir ? NULL : db; /* no divergence for the recursive profile */
-    int rc = sweep(img, a, pa, H, W, 0, S, K, h, g, profile, beta, nthreads);
+    int rc = sweep(img, a, da, H, W, 0, S, K, h, g, profile, beta, nthreads);
     if (fr) memcpy(fr, a, sizeof(double) * (size_t)n);
-    if (rc == 0) rc = sweep(a, b, pa, H, W, 1, S, K, h, g, profile, beta, nthreads);
+    if (rc == 0) rc = sweep(a, b, da, H, W, 1, S, K, h, g, profile, beta, nthreads);
     if (frc) memcpy(frc, b, sizeof(double) * (size_t)n);
     if (d1) memcpy(d1, da, sizeof(double) * (size_t)n);
-    if (rc == 0) rc = sweep(img, a, pb, H, W, 1, S, K, h, g, profile, beta, nthreads);
+    if (rc == 0) rc = sweep(img, a, db, H, W, 1, S, K, h, g, profile, beta, nthreads);
     if (fc) memcpy(fc, a, sizeof(double) * (size_t)n);
-    if (rc == 0) rc = sweep(a, b, pb, H, W, 0, S, K, h, g, profile, beta, nthreads);
+    if (rc == 0) rc = sweep(a, b, db, H, W, 0, S, K, h, g, profile, beta, nthreads);
     if (fcr) memcpy(fcr, b, sizeof(double) * (size_t)n);
     if (d2) memcpy(d2, db, sizeof(double) * (size_t)n);
     free(a); free(b); free(da); free(db);

@@ -220,9 +220,47 @@ def test_rejections(orc):
     with pytest.raises(ValueError):
         orc.patch_dist_1d(x, 2, 0, "gauss_iir", 0.4)        # below the published range of the q rule
     with pytest.raises(ValueError):
-        orc.nlm_1d(x, 2, 0, 1.0, "gauss_iir", 1.0, with_delta=True)   # no divergence for this profile
-    with pytest.raises(ValueError):
-        orc.snlm(np.zeros((4, 4)), 2, 2, 1.0, "gauss_iir", 1.0, order="SURE", sigma=1.0)
+        orc.nlm_1d(x, 2, 0, 1.0, "gauss_iir", 70.0)
+
+
+# ---------------------------------------------------------------- divergence (Eq. (24)) and SURE
+
+@pytest.mark.parametrize("S,beta", [(5, 1.5), (8, 2.5), (3, 0.5)])
+def test_divergence_matches_central_differences(orc, S, beta):
+    # Eq. (24) with the recursive profile: centre weight g(0) = beta sqrt(2 pi) h(0)
+    # and the patch term over the whole window. Interior points only: near the ends
+    # f(i) also enters the mirrored samples, which Eq. (24) leaves out.
+    f = synth.signals(1, 220, 20.0, seed=7, dtype="f32")[0].astype(np.float64)
+    h = orc.default_h(20.0, 3, "gauss_iir", beta)
+    _, dlt = orc.nlm_1d(f, S, 3, h, "gauss_iir", beta, with_delta=True)
+    eps = 1e-3
+    for i in range(90, 130):
+        fp = f.copy(); fp[i] += eps
+        fm = f.copy(); fm[i] -= eps
+        num = (orc.nlm_1d(fp, S, 3, h, "gauss_iir", beta)[i] - orc.nlm_1d(fm, S, 3, h, "gauss_iir", beta)[i]) / (2 * eps)
+        assert abs(dlt[i] - num) <= 1e-6 * max(1.0, abs(num)), (i, dlt[i], num)
+
+
+def test_sure_theta_minimises_phi(orc):
+    from scipy import optimize
+
+    sigma, S, beta = 25.0, 5, 1.5
+    img = synth.noisy_image(40, 48, sigma, seed=3, dtype="f32").astype(np.float64)
+    h = orc.default_h(sigma, 3, "gauss_iir", beta)
+    out, info = orc.snlm(img, S, 3, h, "gauss_iir", beta, order="SURE", sigma=sigma)
+    pr = orc.snlm_parts(img, S, 3, h, "gauss_iir", beta)
+
+    def phi(theta):
+        # Eq. (17) with Eqs. (14) and (18)
+        ft = theta[0] * pr["frc"] + theta[1] * pr["fcr"]
+        n = img.size
+        return np.sum((ft - img) ** 2) / n - sigma ** 2 + 2 * sigma ** 2 / n * np.sum(theta[0] * pr["d1"] +
+                                                                                      theta[1] * pr["d2"])
+
+    res = optimize.minimize(phi, x0=np.array([0.5, 0.5]), method="BFGS", options=dict(gtol=1e-12, maxiter=2000))
+    th = np.array([info["theta1"], info["theta2"]])
+    assert phi(th) <= res.fun + 1e-9 * abs(res.fun) + 1e-12
+    np.testing.assert_allclose(out, th[0] * pr["frc"] + th[1] * pr["fcr"], rtol=1e-14, atol=1e-11)
 
 
 def test_nlm_of_a_step_matches_its_closed_form(orc):
