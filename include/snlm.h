@@ -247,10 +247,12 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
  * (held by every device that loads the library until the process exits).
  *  - Images that need more scratch are rejected with SNLM_ERR_ARG before any work
  *    is queued; snlm_workspace_bytes(H, W, order) <= SNLM_NOALLOC_SCRATCH_BYTES is
- *    a sufficient condition (e.g. SURE up to about 1400 x 1400, RC up to about
- *    2800 x 2800).
- *  - The first call on a device looks up the scratch area's device address; make
- *    that first call before capturing any stream.
+ *    a sufficient condition. The largest square images it admits for every S are
+ *    1654 x 1654 (SURE), 2047 x 2047 (AVG) and 2896 x 2896 (RC, CR).
+ *  - Every call looks up the scratch area's device address in the context that is
+ *    current (a host-side query, so a reset device or another context on the same
+ *    device is handled). The first call in a context may load the library's device
+ *    code; make that first call before capturing any stream.
  *  - All calls in the process share the scratch area. Calls whose device work can
  *    overlap in time (several streams, or several host threads without ordering)
  *    race on it and corrupt each other's results: serialise them.
@@ -351,6 +353,21 @@ typedef enum {
 int snlm_trace_enable(int enable);
 int snlm_trace_read(int *kinds, float *ms, int max_records, int *n_records);
 const char *snlm_kernel_name(int kind);
+
+/*
+ * Measured arithmetic peaks of the current device (no counterpart in the paper; a
+ * measurement aid for the roofline of the 1-D passes, which are bound by FP32
+ * issue). Runs three short kernels on `stream` (cudaStream_t as void*, NULL for the
+ * default stream), each of independent dependency chains in every thread of a grid
+ * of 8 CTAs of 256 threads per SM, timed with CUDA events over 3 launches after
+ * one warm-up launch, and waits for them. On return rates[0] = FP32 lane-operations
+ * per second issued as packed FP32x2 FMAs, rates[1] = the same through scalar FMAs
+ * (an FMA counts as one lane-operation, as in the roofline's operation count),
+ * rates[2] = MUFU.EX2 results per second. `rates` is a HOST array of 3 doubles.
+ * Takes a few tens of milliseconds. Returns SNLM_ERR_ARG for a NULL `rates`,
+ * SNLM_ERR_CUDA when a launch or an event fails.
+ */
+int snlm_probe_peaks(double *rates, void *stream);
 
 /*
  * Serving loop (no counterpart in the paper): continuous batching of requests

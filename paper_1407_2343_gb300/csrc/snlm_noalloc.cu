@@ -15,8 +15,6 @@
 // every CTA writes its own partial-sum record. Two calls whose device work
 // overlaps in time (different streams, or different host threads without
 // ordering) race on the array and corrupt each other's results; serialise them.
-#include <mutex>
-
 #include <cuda_runtime.h>
 
 #include "../../include/snlm.h"
@@ -24,12 +22,9 @@
 namespace {
 
 // Fixed scratch of snlm_denoise_noalloc (32 MiB). Every device that loads the
-// library holds it until the process exits.
+// library holds it until the process exits. Host code sees only a stand-in for
+// this symbol; its device address is looked up on every call (below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SNLM_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -37,28 +32,16 @@ extern "C" int snlm_denoise_noalloc(const void *img, int dtype, int H, int W, in
                                     float h, int profile, int order, float sigma, float beta, float *out,
                                     void *stream)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    // Where the static array lives in the memory of the device (and context) that
+    // is current now. A static __device__ array has one copy per context, so the
+    // address is not cached: after cudaDeviceReset, or with another context made
+    // current on the same device, a remembered address would point at freed or
+    // foreign memory. The lookup is a host-side query; no device work is queued.
+    void *scratch = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+    if (e != cudaSuccess || !scratch) {
         cudaGetLastError();
         return SNLM_ERR_CUDA;
-    }
-    if (dev < 0 || dev >= kMaxDevices)
-        return SNLM_ERR_UNSUPPORTED;
-    void *scratch = nullptr;
-    {
-        // First call on this device: look up where the static array lives in the
-        // device's memory (host code only knows a host-side stand-in symbol).
-        std::lock_guard<std::mutex> g(g_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                cudaGetLastError();
-                return SNLM_ERR_CUDA;
-            }
-            g_addr[dev] = p;
-        }
-        scratch = g_addr[dev];
     }
     // The regular entry point with caller-provided scratch does the rest; it
     // rejects an image whose scratch would not fit (SNLM_ERR_ARG) before any launch
