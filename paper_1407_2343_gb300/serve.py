@@ -95,8 +95,7 @@ def make_schedule(n: int, rate: float, seed: int = 0, sizes=SIZES, weights=SIZE_
         profile = str(rng.choice(["box", "gauss"]))
         order = str(rng.choice(["RC", "CR", "AVG", "SURE"]))
         beta = K / 2.0
-        g = np.exp(-(np.arange(-K, K + 1) ** 2) / (2.0 * beta * beta)) if profile == "gauss" else np.ones(2 * K + 1)
-        h = float(sigma * math.sqrt(g.sum()))   # the default rule h = sigma sqrt(sum_k g(k))
+        h = api.snlm_default_h(sigma, K, profile, beta)   # the library's default rule
         reqs.append(Request(i, img, S, K, h, profile, order, sigma, beta, t))
     return reqs
 

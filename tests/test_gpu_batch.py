@@ -1,8 +1,11 @@
-"""Batched persistent launches (snlm_batch_*) against the per-image entry point.
+"""Batched persistent launches (snlm_batch_*) against the FP64 oracle and the
+per-image entry point.
 
-RC, CR and AVG results must equal snlm_denoise's bit for bit (each unit runs the
-same code on the same data); SURE results within the 1e-4 tolerance (the per-image
-sums are reduced in a different fixed order, so theta may differ in its last bits).
+Every batched output, SURE included, is compared with the oracle's Alg. 4 on the
+same stored samples within the 1e-4 tolerance. Against snlm_denoise, RC, CR and
+AVG results must be equal bit for bit (each unit runs the same code on the same
+data); SURE results within 1e-4 (the per-image sums are reduced in a different
+fixed order, so theta may differ in its last bits).
 """
 import numpy as np
 import pytest
@@ -61,7 +64,17 @@ MIXED = [dict(H=64, W=90, dtype="u8", sigma=20, S=5, K=2),
          dict(H=200, W=180, dtype="u8", sigma=35, S=12, K=5)]
 
 
-def check(reqs):
+def oracle_out(r):
+    """Alg. 4 of the FP64 oracle on the request's stored samples."""
+    import oracle
+
+    oracle.build()
+    f = r["img"].cpu().numpy().astype(np.float64)
+    out, _ = oracle.snlm(f, r["S"], r["K"], r["h"], r["profile"], r["beta"], order=r["order"], sigma=r["sigma"])
+    return out
+
+
+def check(reqs, with_oracle=True):
     for r in reqs:
         ref = reference(r).cpu().numpy()
         got = r["out"].cpu().numpy()
@@ -69,6 +82,9 @@ def check(reqs):
             assert np.abs(got - ref).max() <= TOL, (r["img"].shape, r["order"])
         else:
             assert np.array_equal(got, ref), (r["img"].shape, r["order"], np.abs(got - ref).max())
+        if with_oracle:
+            err = float(np.abs(got.astype(np.float64) - oracle_out(r)).max())
+            assert err <= TOL, (r["img"].shape, r["order"], r["profile"], err)
 
 
 def test_batch_matches_per_image(dev):
@@ -123,13 +139,16 @@ def test_batch_graph_replay(dev):
 
 def test_batch_uneven_workload_recipe(dev):
     # 40 images drawn from the uneven batch recipe (sides 64..1024, u8/f16, S in
-    # {5,10,15}, K in {2,3,5}, box, RC)
+    # {5,10,15}, K in {2,3,5}, box), the four orders of Alg. 4 in turn, each
+    # against the per-image path and the oracle
     import torch
 
     from paper_1407_2343_gb300 import api
     from paper_1407_2343_gb300.batch import Batch
 
     specs = synth.batch_specs(40, seed=1)
+    for i, sp in enumerate(specs):          # every order of Alg. 4 in the mix
+        sp["order"] = ("RC", "CR", "AVG", "SURE")[i % 4]
     reqs = make_requests(dev, specs)
     b = Batch(reqs, queue_order=1)
     b.capture()

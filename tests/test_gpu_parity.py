@@ -311,46 +311,33 @@ def test_argument_errors_leave_output_untouched(dev, api):
     assert bool((out == 7.0).all())
 
 
-def test_full_size_sampled_parity(dev, api, orc):
+def test_full_size_whole_image_parity(dev, api, orc):
     # 4096x4096 uint8, S = 20, K = 5, box, sigma = 30: the benchmark's launch
-    # configuration. f_rc and f_cr at sampled pixels are compared with the oracle
-    # run on a crop large enough that its own borders cannot reach the sample
-    # (an output pixel depends on inputs within S + K in each direction, twice);
-    # the SURE output is then checked against theta and the reported sums.
+    # configuration, compared with the oracle over the whole image. RC and CR
+    # element by element, the SURE output element by element, and the SURE system
+    # of Alg. 4: theta and the seven sums of Eqs. (19) and (25).
     import torch
 
     H = W = 4096
     S, K, sigma = 20, 5, 30.0
-    R = S + K
     img = synth.noisy_image(H, W, sigma, seed=0, dtype="u8")
     t = to_dev(img, dev)
     h = orc.default_h(sigma, K)
-    rc = np_of(api.snlm_denoise(t, S, K, h, "box", "RC"))
-    cr = np_of(api.snlm_denoise(t, S, K, h, "box", "CR"))
-    info = torch.zeros(10, dtype=torch.float64, device=dev)
-    sure = np_of(api.snlm_denoise_ws(t, S, K, h, "box", "SURE", sigma, info=info))
-    gi = np_of(info)
-    rng = np.random.default_rng(0)
-    pts = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0), (7, 2000), (3000, 4090)]
-    pts += [tuple(p) for p in rng.integers(0, 4096, size=(10, 2))]
-    for (r, c) in pts:
-        r0, c0 = max(0, r - 2 * R), max(0, c - 2 * R)
-        r1, c1 = min(H, r + 2 * R + 1), min(W, c + 2 * R + 1)
-        crop = img[r0:r1, c0:c1].astype(np.float64)
-        parts = orc.snlm_parts(crop, S, K, h)
-        assert abs(rc[r, c] - parts["frc"][r - r0, c - c0]) <= TOL
-        assert abs(cr[r, c] - parts["fcr"][r - r0, c - c0]) <= TOL
-    # the SURE output is theta1 f_rc + theta2 f_cr with theta from the reported sums
-    assert np.abs(sure - (gi[0] * rc.astype(np.float64) + gi[1] * cr.astype(np.float64))).max() <= TOL
     f = img.astype(np.float64)
-    assert gi[2] == pytest.approx(np.sum(rc.astype(np.float64) ** 2), rel=1e-6)
-    assert gi[3] == pytest.approx(np.sum(rc.astype(np.float64) * cr.astype(np.float64)), rel=1e-6)
-    assert gi[4] == pytest.approx(np.sum(cr.astype(np.float64) ** 2), rel=1e-6)
-    assert gi[5] == pytest.approx(np.sum(f * rc), rel=1e-6)
-    assert gi[6] == pytest.approx(np.sum(f * cr), rel=1e-6)
-    det = gi[2] * gi[4] - gi[3] ** 2
-    b0, b1 = gi[5] - sigma ** 2 * gi[7], gi[6] - sigma ** 2 * gi[8]
-    assert gi[0] == pytest.approx((gi[4] * b0 - gi[3] * b1) / det, rel=1e-9, abs=1e-9)
+    for order in ("RC", "CR"):
+        got = np_of(api.snlm_denoise(t, S, K, h, "box", order)).astype(np.float64)
+        ref, _ = orc.snlm(f, S, K, h, "box", order=order)
+        err = float(np.abs(got - ref).max())
+        assert err <= TOL, (order, err)
+    info = torch.zeros(10, dtype=torch.float64, device=dev)
+    sure = np_of(api.snlm_denoise_ws(t, S, K, h, "box", "SURE", sigma, info=info)).astype(np.float64)
+    gi = np_of(info)
+    ref, ri = orc.snlm(f, S, K, h, "box", order="SURE", sigma=sigma)
+    err = float(np.abs(sure - ref).max())
+    assert err <= TOL, err
+    assert abs(gi[0] - ri["theta1"]) <= 1e-6 and abs(gi[1] - ri["theta2"]) <= 1e-6, (gi[:2], ri)
+    for k, name in enumerate(["A11", "A12", "A22", "sum_f_frc", "sum_f_fcr", "sum_d1", "sum_d2"]):
+        assert gi[2 + k] == pytest.approx(ri[name], rel=1e-5), name
     # patch distances of the first rows, bit exact
     d = np_of(api.snlm_patch_dist_1d(t[:4], S, K, "box"))
     np.testing.assert_array_equal(d, orc.patch_dist_1d(img[:4].astype(np.float64), S, K, "box").astype(np.int64))

@@ -1,8 +1,9 @@
 """The continuous-batching service (the Python loop `Server` and the library's own
 loop `NativeServer`): schedule generation (CPU), and on the GPU the result of every
-request alone equals its result in the mix, launches overlap, admission under a
-memory cap, the plain (one request at a time) mode, and rejection of a request
-larger than the whole budget."""
+request alone equals its result in the mix, every served result of a mixed schedule
+(sizes up to 512^2, every order, both profiles, u8 and f16 storage) is within 1e-4
+of the FP64 oracle, launches overlap, admission under a memory cap, the plain (one
+request at a time) mode, and rejection of a request larger than the whole budget."""
 import math
 
 import numpy as np
@@ -39,6 +40,16 @@ def dev():
     build.build()
     _lib.load()
     return torch.device("cuda:0")
+
+
+def oracle_out(r):
+    """Alg. 4 of the FP64 oracle on the request's stored samples."""
+    import oracle
+
+    oracle.build()
+    f = r.img.numpy().astype(np.float64)
+    out, _ = oracle.snlm(f, r.S, r.K, r.h, r.profile, r.beta, order=r.order, sigma=r.sigma)
+    return out
 
 
 def alone(r, dev):
@@ -104,6 +115,22 @@ def test_native_server_results_alone_equal_results_in_the_mix(dev):
         assert r.t_done >= r.t_arrival
     s = stats.summary()
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_served_results_match_the_oracle(dev, mode):
+    # a burst of mixed requests (128^2 to 512^2; S, K, profile, order and storage
+    # drawn per request), served by the native loop, every result against the oracle
+    reqs = serve.make_schedule(32, rate=50000.0, seed=11, sizes=(128, 256, 512), weights=(0.4, 0.35, 0.25))
+    stats = serve.NativeServer(mode).run(reqs)
+    assert stats.images == len(reqs)
+    if mode == "batched":
+        assert stats.max_batch > 1
+    assert {r.order for r in reqs} == {"RC", "CR", "AVG", "SURE"}
+    for r in reqs:
+        err = float(np.abs(r.out.numpy().astype(np.float64) - oracle_out(r)).max())
+        assert err <= TOL, (r.rid, r.shape, r.order, r.profile, r.S, r.K, err)
 
 
 @pytest.mark.gpu
