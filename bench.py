@@ -112,9 +112,12 @@ def parse():
     ap.add_argument("--no-nlm2d", action="store_true", help="skip the 2-D NLM comparison")
     ap.add_argument("--no-3d", action="store_true", help="skip the separable 3-D extension measurement")
     ap.add_argument("--no-iir", action="store_true", help="skip the recursive Gaussian profile measurement")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the fp16-storage measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-configuration error table")
     ap.add_argument("--batch-images", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sweep")
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-repeats", type=int, default=3)
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the benchmark line, time Alg. 4 over S (K = 3) and K (S = 20), "
                          "box and Gaussian, and print one JSON line")
@@ -187,24 +190,25 @@ class Clocks:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(a, target_s: float):
+def cpu_oracle_rate(a, target_s: float, nthreads: int = 0):
     """Time the FP64 oracle (as it stands) on a bounded crop of the workload's
-    scene on the host cores; returns (Mpixel/s, cores, description)."""
+    scene on the host cores (all of them, or `nthreads`); returns (Mpixel/s, cores,
+    description, side, seconds)."""
     import oracle
     from paper_1407_2343_gb300 import synth
 
     oracle.build()
     img = synth.noisy_image(a.size, a.size, a.sigma, seed=0, dtype=a.dtype).astype(np.float64)
     h = oracle.default_h(a.sigma, a.K, a.profile)
-    cores = oracle.max_threads()
-    side = 128
+    cores = nthreads or oracle.max_threads()
+    side = 128 if cores > 1 else 64
     t0 = time.perf_counter()
-    oracle.snlm(img[:side, :side], a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    oracle.snlm(img[:side, :side], a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma, nthreads=cores)
     t_cal = time.perf_counter() - t0
-    side = int(min(a.size, max(128, side * math.sqrt(target_s / max(t_cal, 1e-4)))))
+    side = int(min(a.size, max(64, side * math.sqrt(target_s / max(t_cal, 1e-4)))))
     crop = img[:side, :side]
     t0 = time.perf_counter()
-    oracle.snlm(crop, a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma)
+    oracle.snlm(crop, a.S, a.K, h, a.profile, order=a.order, sigma=a.sigma, nthreads=cores)
     dt = time.perf_counter() - t0
     return side * side / dt / 1e6, cores, f"{side}x{side} top-left crop of the same scene, one Alg. 4 run ({dt:.2f} s)", side, dt
 
@@ -428,6 +432,103 @@ def psnr(x, clean):
     return 10.0 * math.log10(255.0 ** 2 / mse)
 
 
+def measure_precision(a, dev):
+    """Error of the library against the FP64 oracle, stated per configuration (max-abs
+    and mean-abs of the float32 output on the [0, 255] scale; PSNR against the clean
+    scene for information):
+    - every cell of the 512^2 float32 configuration: sigma in {10, 20, 30, 50} x
+      profile {box, Gaussian beta = K/2} x K in {2, 3, 5} x order {RC, CR, AVG,
+      SURE}, S = 10, h from the default rule;
+    - the large single images in uint8 and float16 storage, 2048^2 and 4096^2, S in
+      {10, 20}, K in {3, 5}, box, sigma = 30, SURE order (all four passes), whole
+      images."""
+    import torch
+
+    import oracle
+    from paper_1407_2343_gb300 import api, synth
+
+    oracle.build()
+    t0 = time.perf_counter()
+    cfg2 = []
+    for sigma in (10.0, 20.0, 30.0, 50.0):
+        sc = synth.scene(512, 512, sigma, seed=int(sigma))
+        f = synth.store(sc.noisy, "f32")
+        t = torch.from_numpy(f).to(dev)
+        for prof in ("box", "gauss"):
+            for K in (2, 3, 5):
+                h = api.snlm_default_h(sigma, K, prof, K / 2.0)
+                for order in ("RC", "CR", "AVG", "SURE"):
+                    got = api.snlm_denoise(t, 10, K, h, prof, order, sigma, K / 2.0).cpu().numpy().astype(np.float64)
+                    ref, _ = oracle.snlm(f.astype(np.float64), 10, K, h, prof, K / 2.0, order=order, sigma=sigma)
+                    d = np.abs(got - ref)
+                    cfg2.append({"sigma": sigma, "profile": prof, "K": K, "order": order,
+                                 "max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                                 "psnr_db": psnr(got, sc.clean)})
+    cfg3 = []
+    for n in (2048, 4096):
+        sc = synth.scene(n, n, 30.0, seed=0)
+        for dt in ("u8", "f16"):
+            f = synth.store(sc.noisy, dt)
+            t = torch.from_numpy(f).to(dev)
+            for S in (10, 20):
+                for K in (3, 5):
+                    h = api.snlm_default_h(30.0, K)
+                    got = api.snlm_denoise(t, S, K, h, "box", "SURE", 30.0).cpu().numpy().astype(np.float64)
+                    ref, _ = oracle.snlm(f.astype(np.float64), S, K, h, "box", order="SURE", sigma=30.0)
+                    d = np.abs(got - ref)
+                    cfg3.append({"size": n, "storage": dt, "S": S, "K": K, "order": "SURE",
+                                 "max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                                 "psnr_db": psnr(got, sc.clean)})
+            del t
+    worst = max(c["max_abs"] for c in cfg2 + cfg3)
+    return {"tolerance": 1e-4, "worst_max_abs": worst, "cells": len(cfg2) + len(cfg3),
+            "config_512_f32": cfg2, "large_u8_f16_sure": cfg3, "seconds": time.perf_counter() - t0}
+
+
+def measure_storage(a, api, dev, stream, flush, dtype):
+    """The benchmark's step (same scene, S, K, order) with the image stored as
+    `dtype`: device time per step and the dominant pass's ALU fraction."""
+    import torch
+
+    from paper_1407_2343_gb300 import synth
+
+    n = a.size
+    img = torch.from_numpy(synth.noisy_image(n, n, a.sigma, seed=0, dtype=dtype)).to(dev)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    ws = torch.empty(api.snlm_workspace_bytes(n, n, a.order), dtype=torch.uint8, device=dev)
+    h = api.snlm_default_h(a.sigma, a.K, a.profile)
+
+    def step():
+        api.snlm_denoise_ws(img, a.S, a.K, h, a.profile, a.order, a.sigma, out=out, workspace=ws, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    reps = max(10, min(50, a.steps // 8))
+    api.snlm_trace_read()
+    api.snlm_trace_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    api.snlm_trace_enable(False)
+    per = {}
+    for name, ms in api.snlm_trace_read(1 << 20):
+        per.setdefault(name, []).append(ms)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+    dom = max(per.items(), key=lambda kv: sum(kv[1]))[0]
+    avg = float(np.mean(per[dom])) * 1e-3
+    kind = "sure" if "_sure" in dom else "plain"
+    ach = OPS_PER_PAIR[kind] * n * n * a.S / avg / 1e12
+    return {"storage": dtype, "ms_per_step": ms, "Mpixel_s": n * n / (ms * 1e-3) / 1e6,
+            "dominant_kernel": dom, "dominant_avg_ms": avg * 1e3, "achieved_Tops": ach,
+            "frac_of_nominal": ach / ALU_PEAK_TOPS,
+            "kernels_ms": {k: float(np.mean(v)) for k, v in per.items()}}
+
+
 def measure_batched(a, dev, stream):
     """The uneven batch: images with sides log-uniform in [64, 1024], aspect in
     [1/2, 2], u8/f16, sigma ~ U[10, 50], S in {5,10,15}, K in {2,3,5}, box, RC.
@@ -488,56 +589,83 @@ def measure_batched(a, dev, stream):
 
 
 def measure_served(a, dev):
-    """Poisson arrivals swept from 0.2x to 1.5x of the plain path's capacity;
-    sizes {128, 512, 1024, 2048, 4096}^2 with weights {.3, .3, .2, .15, .05}; each
-    request with its own S, K, h, profile and order. The library's serving loop in
+    """Poisson arrivals swept from 0.2x to 3x of the plain path's capacity; sizes
+    {128, 512, 1024, 2048, 4096}^2 with weights {.3, .3, .2, .15, .05}; each request
+    with its own S, K, h, profile and order. The library's serving loop in
     continuous-batching mode against its plain mode (one request at a time through
     the per-image path) on the same schedule; latency is arrival to result in host
-    memory. Accuracy: the served results against the plain ones
-    (all requests) and against the FP64 oracle (a sample of small requests)."""
+    memory. Each point runs `serve_requests` requests `serve_repeats` times (fresh
+    schedules, seeds 6, 7, ...); the median and the range over the repeats are
+    reported. The timing schedules write their results into a ring of 8 host buffers
+    per size (requests of one size share them, so their contents are not checked);
+    accuracy is checked on a separate schedule with a buffer per request: served
+    against plain (all requests) and against the FP64 oracle (every request up to
+    512^2)."""
     import numpy as np
+    import torch
 
     import oracle
     from paper_1407_2343_gb300 import serve
 
-    n = a.serve_requests
+    n, reps = a.serve_requests, a.serve_repeats
     pool = serve.make_pool()
+    ring = {sz: [torch.empty((sz, sz), dtype=torch.float32).pin_memory() for _ in range(8)] for sz in serve.SIZES}
+
+    def schedule(rate, seed, count=n):
+        sched = serve.make_schedule(count, rate=rate, seed=seed, pool=pool)
+        used = {}
+        for r in sched:
+            k = used.get(r.shape[0], 0)
+            r.out = ring[r.shape[0]][k % 8]
+            used[r.shape[0]] = k + 1
+        return sched
+
     plain_srv, served_srv = serve.NativeServer("plain"), serve.NativeServer("batched")
     # warm-up of both loops (module loading and kernel attributes of every variant)
     for srv in (plain_srv, served_srv):
-        srv.run(serve.prepare_outputs(serve.make_schedule(n, rate=1e9, seed=4, pool=pool)))
+        srv.run(schedule(1e9, 4, min(n, 400)))
     # capacity of the plain path: everything arrives at once (best of two runs)
     cap = 0.0
-    for _ in range(2):
-        sched = serve.make_schedule(n, rate=1e9, seed=5, pool=pool)
-        serve.prepare_outputs(sched)
-        cap = max(cap, plain_srv.run(sched).summary()["images_per_s"])
+    for k in range(2):
+        cap = max(cap, plain_srv.run(schedule(1e9, 5 + k)).summary()["images_per_s"])
     sweep = []
-    worst_vs_plain = 0.0
-    served_ref = None
     for frac in (0.2, 0.5, 1.0, 1.5, 2.0, 3.0):
         rate = frac * cap
-        sp = serve.prepare_outputs(serve.make_schedule(n, rate=rate, seed=6, pool=pool))
-        ss = serve.prepare_outputs(serve.make_schedule(n, rate=rate, seed=6, pool=pool))
-        p = plain_srv.run(sp).summary()
-        s = served_srv.run(ss).summary()
-        for x, y in zip(sp, ss):
-            worst_vs_plain = max(worst_vs_plain, float(np.abs(x.out.numpy() - y.out.numpy()).max()))
-        sweep.append({"rate_frac_of_plain_capacity": frac, "rate_per_s": rate, "plain": p, "served": s})
-        served_ref = ss
-    # oracle on a sample of the small requests of the last schedule
+        runs = {"plain": [], "served": []}
+        for rep in range(reps):
+            for mode, srv in (("plain", plain_srv), ("served", served_srv)):
+                runs[mode].append(srv.run(schedule(rate, 6 + rep)).summary())
+        pt = {"rate_frac_of_plain_capacity": frac, "rate_per_s": rate}
+        for mode in ("plain", "served"):
+            agg = {}
+            for key in ("images_per_s", "p50_ms", "p99_ms", "mean_ms"):
+                v = [r[key] for r in runs[mode]]
+                agg[key] = float(np.median(v))
+                agg[key + "_range"] = [float(min(v)), float(max(v))]
+            agg["max_batch"] = max(r["max_batch"] for r in runs[mode])
+            agg["max_inflight_steps"] = max(r["max_inflight_steps"] for r in runs[mode])
+            pt[mode] = agg
+        sweep.append(pt)
+    # accuracy: a separate schedule at 2x capacity, one result buffer per request
+    n_acc = 120
+    sp = serve.prepare_outputs(serve.make_schedule(n_acc, rate=2 * cap, seed=99, pool=pool))
+    ss = serve.prepare_outputs(serve.make_schedule(n_acc, rate=2 * cap, seed=99, pool=pool))
+    plain_srv.run(sp)
+    served_srv.run(ss)
+    worst_vs_plain = max(float(np.abs(x.out.numpy() - y.out.numpy()).max()) for x, y in zip(sp, ss))
     worst_vs_oracle, checked = 0.0, 0
-    for r in served_ref:
-        if r.shape[0] > 512 or checked >= 4:
+    for r in ss:
+        if r.shape[0] > 512:
             continue
         ref, _ = oracle.snlm(r.img.numpy().astype(np.float64), r.S, r.K, r.h, r.profile, r.beta, r.order, r.sigma)
         worst_vs_oracle = max(worst_vs_oracle, float(np.abs(r.out.numpy() - ref).max()))
         checked += 1
-    return {"workload": f"{n} requests per point, Poisson arrivals, sizes 128..4096 squared with weights "
-                        ".3/.3/.2/.15/.05, S in {5,10,15,20}, K in {2,3,5}, box/gauss, RC/CR/AVG/SURE, u8/f16",
+    return {"workload": f"{n} requests per point, {reps} repeats (median and range), Poisson arrivals, sizes "
+                        "128..4096 squared with weights .3/.3/.2/.15/.05, S in {5,10,15,20}, K in {2,3,5}, "
+                        "box/gauss, RC/CR/AVG/SURE, u8/f16",
             "plain_capacity_images_per_s": cap, "sweep": sweep,
-            "max_abs_served_vs_plain": worst_vs_plain, "max_abs_served_vs_oracle": worst_vs_oracle,
-            "oracle_checked_requests": checked}
+            "accuracy_schedule_requests": n_acc, "max_abs_served_vs_plain": worst_vs_plain,
+            "max_abs_served_vs_oracle": worst_vs_oracle, "oracle_checked_requests": checked}
 
 
 def run_ours(a):
@@ -571,6 +699,11 @@ def run_ours(a):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    # measured FP32 and MUFU.EX2 rates of this GPU (the library's probe kernels),
+    # taken before the timed region
+    peaks = api.snlm_probe_peaks(stream)
+    fp32_meas = max(peaks["fp32_fma2_ops_s"], peaks["fp32_fma_ops_s"]) / 1e12
+    ex2_meas = peaks["ex2_s"] / 1e12
 
     def timed(order, steps, clocks=None):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -627,13 +760,18 @@ def run_ours(a):
                 "ops_per_unique_pair": OPS_PER_PAIR[kind], "unique_pairs_per_launch": pairs_launch,
                 "avg_launch_ms": avg_s * 1e3,
                 "sfu": {"achieved_Texp_s": pairs_launch / avg_s / 1e12, "peak_Texp_s": SFU_PEAK_TEXP,
-                        "frac": pairs_launch / avg_s / 1e12 / SFU_PEAK_TEXP},
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and maximum clock)"}
+                        "frac": pairs_launch / avg_s / 1e12 / SFU_PEAK_TEXP,
+                        "measured_peak_Texp_s": ex2_meas, "frac_of_measured": pairs_launch / avg_s / 1e12 / ex2_meas},
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and maximum clock)",
+                "measured_peak": fp32_meas, "frac_of_measured": achieved / fp32_meas,
+                "measured_peak_source": "snlm_probe_peaks: independent FMA chains in every thread of 8 CTAs x 256 "
+                                        "threads per SM (best of packed FP32x2 and scalar FMA), CUDA events",
+                "probe": {k: v / 1e12 for k, v in peaks.items()}}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": dev_ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload(a), parallelism=f"replicas{world}" if world > 1 else "single"),
+            "config": workload(a), "parallelism": f"replicas{world}" if world > 1 else "single",
             "pairs_per_s": pairs_paper, "unique_pairs_per_s": pairs_paper * a.S / (2 * a.S + 1),
             "wall_s_timed_region": wall, "roofline": roofline, "kernels": kernels,
             "gpu_launches": len(trace), "clocks": clocks}
@@ -698,15 +836,53 @@ def run_ours(a):
     if not a.no_serve and rank == 0:
         line["served"] = measure_served(a, dev)
 
+    if not a.no_fp16 and rank == 0:
+        line["fp16_storage"] = measure_storage(a, api, dev, stream, flush, "f16")
+
+    if not a.no_precision and rank == 0:
+        line["precision"] = measure_precision(a, dev)
+
     if rank == 0 and not a.no_cpu_baseline:
         v, cores, desc, _, _ = cpu_oracle_rate(a, target_s=6.0)
-        line["cpu_baseline"] = {"value": v, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": desc}
+        v1, _, desc1, _, _ = cpu_oracle_rate(a, target_s=4.0, nthreads=1)
+        line["cpu_baseline"] = {"value": v, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "single_core": {"value": v1, "unit": "Mpixel/s", "cores": 1, "sample": desc1}}
 
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank == 0:
+        print(summary_line(line), flush=True)
         print(json.dumps(line), flush=True)
+
+
+def summary_line(line):
+    """One human-readable line of the headline figures (printed just before the JSON)."""
+    parts = [f"summary: {line['value']:.0f} Mpixel/s ({line['ms_per_step']:.3f} ms/step)",
+             f"dominant {line['roofline']['kernel']} {line['roofline']['avg_launch_ms']:.3f} ms = "
+             f"{line['roofline']['frac']:.3f} of nominal ALU, {line['roofline']['frac_of_measured']:.3f} of measured"]
+    if "e2e" in line:
+        parts.append(f"e2e {line['e2e']['value']:.0f} Mpixel/s")
+    if "fp16_storage" in line:
+        parts.append(f"fp16 {line['fp16_storage']['Mpixel_s']:.0f} Mpixel/s")
+    if "batched" in line:
+        b = line["batched"]
+        parts.append(f"batched {b['batched_images_per_s']:.0f} vs plain {b['plain_images_per_s']:.0f} images/s "
+                     f"({b['speedup']:.2f}x)")
+    if "served" in line:
+        pts = []
+        for p in line["served"]["sweep"]:
+            pts.append(f"{p['rate_frac_of_plain_capacity']:g}x: {p['served']['images_per_s']:.0f}/"
+                       f"{p['plain']['images_per_s']:.0f} img/s p99 {p['served']['p99_ms']:.2f}/"
+                       f"{p['plain']['p99_ms']:.2f} ms")
+        parts.append("served/plain " + "; ".join(pts))
+    if "precision" in line:
+        parts.append(f"worst max-abs vs oracle {line['precision']['worst_max_abs']:.2e} over "
+                     f"{line['precision']['cells']} cells")
+    if "cpu_baseline" in line:
+        parts.append(f"oracle {line['cpu_baseline']['value']:.2f} Mpixel/s on {line['cpu_baseline']['cores']} cores, "
+                     f"{line['cpu_baseline']['single_core']['value']:.3f} on 1")
+    return " | ".join(parts)
 
 
 def run_sweep(a):

@@ -130,6 +130,8 @@ def load(build_if_missing: bool = False):
         lib.snlm_trace_read.restype = ci
         lib.snlm_kernel_name.argtypes = [ci]
         lib.snlm_kernel_name.restype = ctypes.c_char_p
+        lib.snlm_probe_peaks.argtypes = [dp, vp]
+        lib.snlm_probe_peaks.restype = ci
         lib.snlm_set_option.argtypes = [ci, ctypes.c_longlong]
         lib.snlm_set_option.restype = ci
         lib.snlm_get_option.argtypes = [ci]
@@ -165,4 +167,5 @@ EXPORTED = [
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
     "snlm_set_option", "snlm_get_option", "snlm_device_error", "snlm_server_create", "snlm_server_submit",
     "snlm_server_drain", "snlm_server_result", "snlm_server_get_stats", "snlm_server_clock", "snlm_server_destroy",
+    "snlm_probe_peaks",
 ]

@@ -350,6 +350,14 @@ def snlm_kernel_name(kind: int) -> str:
     return _lib.load().snlm_kernel_name(int(kind)).decode()
 
 
+def snlm_probe_peaks(stream=None) -> dict:
+    """Measured FP32 (packed FP32x2 and scalar FMA) lane-operations/s and MUFU.EX2
+    results/s of the current device (see include/snlm.h)."""
+    rates = (ctypes.c_double * 3)()
+    _check(_lib.load().snlm_probe_peaks(rates, _stream_ptr(stream)), "snlm_probe_peaks")
+    return {"fp32_fma2_ops_s": rates[0], "fp32_fma_ops_s": rates[1], "ex2_s": rates[2]}
+
+
 OPT_TMA, OPT_WAIT_LIMIT_US, OPT_INJECT_WAIT_TIMEOUT = 0, 1, 2
 
 
