@@ -237,6 +237,42 @@ int snlm_patch_dist_1d(const void *x, int dtype, int n_lines, int N, int stride,
 
 
 /*
+ * SURE over row bands: the one exchange step when an image is split into bands of
+ * rows (across GPUs or ranks). Alg. 4's divergence and the seven sums of Eqs. (19)
+ * and (25) are sums over pixels, so each band forms its own sums over the rows it
+ * owns, the sums of all bands are added (an all-reduce), and every band solves the
+ * same 2x2 system and combines its own rows.
+ *
+ * snlm_sure_band runs the four passes of Alg. 4 on `img` (a band of a larger image
+ * together with its halo rows, S + K on each side; or any whole image) like
+ * snlm_denoise_ws in the SURE order, but keeps the two orders apart: f_rc (rows then
+ * columns) and f_cr (columns then rows), device float32 H x W (dense, row-major),
+ * and writes to `sums` (device, 7 doubles, 8-byte aligned) the seven sums over the
+ * image rows [row0, row1) only, in the basis m = (f_rc + f_cr)/2,
+ * d = (f_rc - f_cr)/2:
+ *   sums = {sum m^2, sum m d, sum d^2, sum f m, sum f d, sum delta_1, sum delta_2}
+ * (f the stored input samples, delta_1 and delta_2 the chained derivatives of
+ * Eq. (24) of the two orders). The sums of disjoint row sets add. The workspace is
+ * snlm_workspace_bytes(H, W, SNLM_SURE) bytes (16-byte aligned). Errors as
+ * snlm_denoise_ws; SNLM_ERR_ARG also for 0 <= row0 < row1 <= H violated or
+ * f_rc == f_cr. The recursive profile returns SNLM_ERR_UNSUPPORTED.
+ *
+ * snlm_sure_theta solves Eqs. (19), (25) for theta from seven such sums (HOST
+ * arrays; theta: 2 doubles): the minimiser of Eq. (17) in the basis m, d, the
+ * minimum-norm solution when the system is singular (det <= 1e-12 trace^2). It
+ * runs on the host and touches no device.
+ *
+ * snlm_sure_combine writes out = theta1 f_rc + theta2 f_cr over n floats (device
+ * pointers; out may alias f_cr), asynchronously on `stream`.
+ */
+int snlm_sure_band(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
+                   float beta, int row0, int row1, float *f_rc, float *f_cr, double *sums, void *workspace,
+                   size_t workspace_bytes, void *stream);
+int snlm_sure_theta(const double *sums, float sigma, double *theta);
+int snlm_sure_combine(const float *f_rc, const float *f_cr, long long n, double theta1, double theta2, float *out,
+                      void *stream);
+
+/*
  * Separable NLM without any device allocation (no counterpart in the paper).
  * Same computation, arguments and results as snlm_denoise, for callers that may
  * not call cudaMalloc or cudaFree at run time: real-time loops (an allocation can

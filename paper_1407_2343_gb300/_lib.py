@@ -107,6 +107,12 @@ def load(build_if_missing: bool = False):
         lib.snlm_patch_dist_1d.restype = ci
         lib.snlm_denoise_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, ci, cf, cf, vp, vp]
         lib.snlm_denoise_noalloc.restype = ci
+        lib.snlm_sure_band.argtypes = [vp, ci, ci, ci, ci, ci, ci, cf, ci, cf, ci, ci, vp, vp, vp, vp, csz, vp]
+        lib.snlm_sure_band.restype = ci
+        lib.snlm_sure_theta.argtypes = [dp, cf, dp]
+        lib.snlm_sure_theta.restype = ci
+        lib.snlm_sure_combine.argtypes = [vp, vp, cll, ctypes.c_double, ctypes.c_double, vp, vp]
+        lib.snlm_sure_combine.restype = ci
         pp = ctypes.POINTER(ctypes.c_void_p)
         lib.snlm_batch_plan_create.argtypes = [ctypes.POINTER(Request), ci, ctypes.POINTER(BatchConfig), pp]
         lib.snlm_batch_plan_create.restype = ci
@@ -167,5 +173,5 @@ EXPORTED = [
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
     "snlm_set_option", "snlm_get_option", "snlm_device_error", "snlm_server_create", "snlm_server_submit",
     "snlm_server_drain", "snlm_server_result", "snlm_server_get_stats", "snlm_server_clock", "snlm_server_destroy",
-    "snlm_probe_peaks",
+    "snlm_probe_peaks", "snlm_sure_band", "snlm_sure_theta", "snlm_sure_combine",
 ]

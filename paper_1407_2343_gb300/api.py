@@ -375,6 +375,51 @@ def snlm_device_error(stream=None) -> int:
     return int(_lib.load().snlm_device_error(_stream_ptr(stream)))
 
 
+def snlm_sure_band(img, S: int, K: int, h: float | None = None, profile="box", beta: float = 0.0, row0: int = 0,
+                   row1: int | None = None, sigma: float | None = None, f_rc=None, f_cr=None, sums=None,
+                   workspace=None, stream=None):
+    """Alg. 4's four passes of `img` (a band with its halo rows, or a whole image)
+    keeping f_rc and f_cr apart, and the seven SURE sums over rows [row0, row1) in
+    the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2 (see include/snlm.h).
+    Returns (f_rc, f_cr, sums) with sums a float64 CUDA tensor of 7."""
+    torch = _torch()
+    dt, H, W, pitch = _image_args(img)
+    h = _h_for(h, sigma, K, profile, beta)
+    row1 = H if row1 is None else int(row1)
+    f_rc = torch.empty((H, W), dtype=torch.float32, device=img.device) if f_rc is None else f_rc
+    f_cr = torch.empty((H, W), dtype=torch.float32, device=img.device) if f_cr is None else f_cr
+    sums = torch.empty(7, dtype=torch.float64, device=img.device) if sums is None else sums
+    if workspace is None:
+        workspace = torch.empty(snlm_workspace_bytes(H, W, "SURE"), dtype=torch.uint8, device=img.device)
+    rc = _lib.load().snlm_sure_band(_ptr(img), dt, H, W, pitch, int(S), int(K), h, _profile(profile),
+                                    float(beta or 0.0), int(row0), row1, _ptr(f_rc), _ptr(f_cr), _ptr(sums),
+                                    _ptr(workspace), ctypes.c_size_t(workspace.numel()), _stream_ptr(stream))
+    _check(rc, "snlm_sure_band")
+    return f_rc, f_cr, sums
+
+
+def snlm_sure_theta(sums, sigma: float):
+    """theta = (theta1, theta2) of Eqs. (19), (25) from seven sums (host sequence)."""
+    import numpy as np
+
+    arr = (ctypes.c_double * 7)(*[float(x) for x in np.asarray(sums, dtype=np.float64).ravel()[:7]])
+    th = (ctypes.c_double * 2)()
+    _check(_lib.load().snlm_sure_theta(arr, float(sigma), th), "snlm_sure_theta")
+    return float(th[0]), float(th[1])
+
+
+def snlm_sure_combine(f_rc, f_cr, theta, out=None, stream=None):
+    """out = theta1 f_rc + theta2 f_cr (device float32 tensors of the same shape)."""
+    torch = _torch()
+    if f_rc.shape != f_cr.shape or not f_rc.is_contiguous() or not f_cr.is_contiguous():
+        raise ValueError("f_rc and f_cr must be contiguous tensors of one shape")
+    out = torch.empty_like(f_rc) if out is None else out
+    rc = _lib.load().snlm_sure_combine(_ptr(f_rc), _ptr(f_cr), int(f_rc.numel()), float(theta[0]),
+                                       float(theta[1]), _ptr(out), _stream_ptr(stream))
+    _check(rc, "snlm_sure_combine")
+    return out
+
+
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 

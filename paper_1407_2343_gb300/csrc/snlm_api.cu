@@ -10,6 +10,7 @@
 #include "../../include/snlm.h"
 #include "snlm_host.h"
 #include "snlm_internal.h"
+#include "snlm_sure_impl.cuh"
 
 using namespace snlm;
 
@@ -156,7 +157,7 @@ struct Pass {
 };
 
 cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, double h, int profile,
-                     double beta, bool sure, cudaStream_t st)
+                     double beta, bool sure, cudaStream_t st, int sum_lo = 0, int sum_hi = 0)
 {
     PassArgs a;
     memset(&a, 0, sizeof(a));
@@ -176,6 +177,8 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     a.partials = ps.partials;
     a.aux_f = ps.aux_f;
     a.aux_rc = ps.aux_rc;
+    a.sum_lo = sum_lo;
+    a.sum_hi = sum_hi;
     finish_pass_args(a);
     const int dm = dist_mode_for(ps.src.dtype, profile);
     if (dm == DIST_IIR) {
@@ -192,6 +195,41 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
     return tma ? launch_planned_tma(K, a, t, dm, sure, grid, st) : dispatch_pass(K, a, dm, sure, st);
 }
 
+// The four passes of Alg. 4 with the chained divergences: rows then columns into
+// frc (delta_1), columns then rows into fcr (delta_2), with the partial sums of
+// the SURE system restricted to image rows [row0, row1) (row1 == 0: all rows).
+cudaError_t run_sure_passes(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
+                            int profile, double bt, float *frc, float *fcr, const WsLayout &L, char *base,
+                            int row0, int row1, cudaStream_t st)
+{
+    float *tmp = reinterpret_cast<float *>(base + L.tmp);
+    float *delta = reinterpret_cast<float *>(base + L.delta);
+    double *part_rc = reinterpret_cast<double *>(base + L.part_rc);
+    double *part_cr = reinterpret_cast<double *>(base + L.part_cr);
+    const Lines tmp_rows{tmp, DT_F32, (long long)W, 1};
+    const Lines tmp_cols{tmp, DT_F32, 1, (long long)W};
+    cudaError_t e;
+    Pass p1{image_lines(img, dtype, pitch, 0), tmp};
+    p1.delta_out = delta;
+    if ((e = run_pass(0, H, W, p1, S, K, h, profile, bt, true, st, 0, 0)) != cudaSuccess)
+        return e;
+    Pass p2{tmp_cols, frc};
+    p2.delta_in = delta;
+    p2.partials = part_rc;
+    if ((e = run_pass(1, H, W, p2, S, K, h, profile, bt, true, st, row0, row1)) != cudaSuccess)
+        return e;
+    Pass p3{image_lines(img, dtype, pitch, 1), tmp};
+    p3.delta_out = delta;
+    if ((e = run_pass(1, H, W, p3, S, K, h, profile, bt, true, st, 0, 0)) != cudaSuccess)
+        return e;
+    Pass p4{tmp_rows, fcr};
+    p4.delta_in = delta;
+    p4.partials = part_cr;
+    p4.aux_f = image_lines(img, dtype, pitch, 0);
+    p4.aux_rc = Lines{frc, DT_F32, (long long)W, 1};
+    return run_pass(0, H, W, p4, S, K, h, profile, bt, true, st, row0, row1);
+}
+
 int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
                  int profile, int order, float sigma, float beta, float *out, void *ws,
                  double *info, cudaStream_t st)
@@ -200,7 +238,6 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
     char *base = static_cast<char *>(ws);
     float *tmp = reinterpret_cast<float *>(base + L.tmp);
     float *frc = reinterpret_cast<float *>(base + L.frc);
-    float *delta = reinterpret_cast<float *>(base + L.delta);
     double *part_rc = reinterpret_cast<double *>(base + L.part_rc);
     double *part_cr = reinterpret_cast<double *>(base + L.part_cr);
     double *winfo = reinterpret_cast<double *>(base + L.info);
@@ -244,22 +281,7 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         SNLM_TRY(launch_set_theta(winfo, 0.5, 0.5, st));
     } else {
         // Alg. 4: rows then columns with delta_1, columns then rows with delta_2
-        Pass p1{image_lines(img, dtype, pitch, 0), tmp};
-        p1.delta_out = delta;
-        SNLM_TRY(run_pass(0, H, W, p1, S, K, h, profile, bt, true, st));
-        Pass p2{tmp_cols, frc};
-        p2.delta_in = delta;
-        p2.partials = part_rc;
-        SNLM_TRY(run_pass(1, H, W, p2, S, K, h, profile, bt, true, st));
-        Pass p3{image_lines(img, dtype, pitch, 1), tmp};
-        p3.delta_out = delta;
-        SNLM_TRY(run_pass(1, H, W, p3, S, K, h, profile, bt, true, st));
-        Pass p4{tmp_rows, out};
-        p4.delta_in = delta;
-        p4.partials = part_cr;
-        p4.aux_f = image_lines(img, dtype, pitch, 0);
-        p4.aux_rc = Lines{frc, DT_F32, (long long)W, 1};
-        SNLM_TRY(run_pass(0, H, W, p4, S, K, h, profile, bt, true, st));
+        SNLM_TRY(run_sure_passes(img, dtype, H, W, pitch, S, K, h, profile, bt, frc, out, L, base, 0, 0, st));
         {
             TraceScope ts(SNLM_K_SURE_SOLVE, st);
             SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
@@ -338,6 +360,64 @@ int snlm_denoise_ws(const void *img, int dtype, int H, int W, int pitch, int S, 
         return SNLM_ERR_ARG;
     return denoise_core(img, dtype, H, W, pitch, S, K, h, profile, order, sigma, beta, out, workspace,
                         info, static_cast<cudaStream_t>(stream));
+}
+
+int snlm_sure_band(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h, int profile,
+                   float beta, int row0, int row1, float *f_rc, float *f_cr, double *sums, void *workspace,
+                   size_t workspace_bytes, void *stream)
+{
+    int rc = check_denoise(H, W, S, K, h, profile, SNLM_SURE, 0.f, beta);
+    if (rc != SNLM_OK)
+        return rc;
+    if (!valid_dtype(dtype) || pitch < W || (long long)H * pitch >= (1LL << 31))
+        return SNLM_ERR_ARG;
+    if (row0 < 0 || row1 <= row0 || row1 > H)
+        return SNLM_ERR_ARG;
+    if (!is_device_ptr(img) || !is_device_ptr(f_rc) || !is_device_ptr(f_cr) || !is_device_ptr(sums) ||
+        !is_device_ptr(workspace) || f_rc == f_cr)
+        return SNLM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 15) != 0 || (reinterpret_cast<uintptr_t>(sums) & 7) != 0)
+        return SNLM_ERR_ARG;
+    const WsLayout L = ws_layout(H, W, S, SNLM_SURE);
+    if (workspace_bytes < L.total)
+        return SNLM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    const double bt = beta_or_default(beta, K);
+    cudaError_t e = run_sure_passes(img, dtype, H, W, pitch, S, K, h, profile, bt, f_rc, f_cr, L, base, row0, row1,
+                                    st);
+    if (e != cudaSuccess)
+        return status_of(e);
+    TraceScope ts(SNLM_K_SURE_SOLVE, st);
+    e = launch_sure_sums(reinterpret_cast<double *>(base + L.part_rc), (int)pass_ctas(W, H, S),
+                         reinterpret_cast<double *>(base + L.part_cr), (int)pass_ctas(H, W, S), sums,
+                         reinterpret_cast<double *>(base + L.solve), st);
+    return status_of(e);
+}
+
+int snlm_sure_theta(const double *sums, float sigma, double *theta)
+{
+    if (!sums || !theta || !(sigma >= 0.f) || !std::isfinite(sigma))
+        return SNLM_ERR_ARG;
+    for (int k = 0; k < 7; ++k)
+        if (!std::isfinite(sums[k]))
+            return SNLM_ERR_ARG;
+    sure_theta(sums, (double)sigma * sigma, &theta[0], &theta[1]);
+    return SNLM_OK;
+}
+
+int snlm_sure_combine(const float *f_rc, const float *f_cr, long long n, double theta1, double theta2, float *out,
+                      void *stream)
+{
+    if (n < 0 || !std::isfinite(theta1) || !std::isfinite(theta2))
+        return SNLM_ERR_ARG;
+    if (n == 0)
+        return SNLM_OK;
+    if (!is_device_ptr(f_rc) || !is_device_ptr(f_cr) || !is_device_ptr(out))
+        return SNLM_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TraceScope ts(SNLM_K_COMBINE, st);
+    return status_of(launch_combine_theta(f_rc, f_cr, out, n, theta1, theta2, st));
 }
 
 int snlm_denoise(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,

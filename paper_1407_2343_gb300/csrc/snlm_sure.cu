@@ -73,6 +73,35 @@ __global__ void combine_scalar_kernel(const float *__restrict__ frc, float *__re
         out[i] = fmaf(h0, frc[i], fmaf(h1, out[i], fmaf(l0, frc[i], l1 * out[i])));
 }
 
+// The seven sums of a band, in the basis m, d (no solve).
+__global__ void __launch_bounds__(kSolveThreads) sure_sums_kernel(const double *part_rc, int n_rc,
+                                                                  const double *part_cr, int n_cr, double *sums)
+{
+    __shared__ double sh[kPartials * kSolveThreads];
+    double rc[kPartials], cr[kPartials];
+    reduce_records(part_rc, n_rc, sh, rc);
+    reduce_records(part_cr, n_cr, sh, cr);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k)
+            sums[k] = cr[k];
+        sums[5] = rc[5];
+        sums[6] = cr[5];
+    }
+}
+
+// out = theta1 frc + theta2 fcr (theta split into float hi + lo parts).
+__global__ void combine_theta_kernel(const float *__restrict__ frc, const float *fcr, float *out, long long n,
+                                     double t0, double t1)
+{
+    const float h0 = (float)t0, h1 = (float)t1;
+    const float l0 = (float)(t0 - (double)h0), l1 = (float)(t1 - (double)h1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = frc[i], b = fcr[i];
+        out[i] = fmaf(h0, a, fmaf(h1, b, fmaf(l0, a, l1 * b)));
+    }
+}
+
 __global__ void set_theta_kernel(double *info, double t0, double t1)
 {
     if (threadIdx.x < 10)
@@ -117,6 +146,34 @@ cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info,
             blocks = (long long)sms * 8;
         combine_scalar_kernel<<<(unsigned)blocks, 256, 0, st>>>(frc, out_fcr, info, n4 * 4, n);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sure_sums(const double *part_rc, int n_rc, const double *part_cr, int n_cr, double *sums,
+                             double *scratch, cudaStream_t st)
+{
+    const int per_rc = (n_rc + kSolveBlocks - 1) / kSolveBlocks;
+    const int per_cr = (n_cr + kSolveBlocks - 1) / kSolveBlocks;
+    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_rc, n_rc, per_rc, scratch);
+    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_cr, n_cr, per_cr,
+                                                                scratch + kSolveBlocks * kPartials);
+    sure_sums_kernel<<<1, kSolveThreads, 0, st>>>(scratch, kSolveBlocks, scratch + kSolveBlocks * kPartials,
+                                                  kSolveBlocks, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out, long long n, double theta1,
+                                 double theta2, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (n + 255) / 256;
+    if (blocks > (long long)sms * 8)
+        blocks = (long long)sms * 8;
+    combine_theta_kernel<<<(unsigned)blocks, 256, 0, st>>>(frc, fcr, out, n, theta1, theta2);
     return cudaGetLastError();
 }
 

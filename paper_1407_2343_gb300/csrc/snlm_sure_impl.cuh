@@ -33,7 +33,7 @@ __device__ __forceinline__ void reduce_records(const double *part, int n, double
 
 // Minimum-norm solution of the symmetric 2x2 system [a c; c e] t = b: Cramer's
 // rule when det > 1e-12 trace^2, else the projection on the dominant eigenvector.
-__device__ __forceinline__ void solve2_sym(double a, double c, double e, double b0, double b1, double *t0, double *t1)
+__host__ __device__ inline void solve2_sym(double a, double c, double e, double b0, double b1, double *t0, double *t1)
 {
     const double det = a * e - c * c, tr = a + e;
     if (det > 1e-12 * tr * tr) {
@@ -75,17 +75,27 @@ __device__ __forceinline__ void solve2_sym(double a, double c, double e, double 
 // theta and the reported sums from the reduced records of the last pass of each
 // order, solved in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2 (see the
 // solve kernel in snlm_sure.cu for why).
+// theta of Eqs. (19), (25) from the seven sums in the basis m, d:
+// {sum m^2, sum m d, sum d^2, sum f m, sum f d, sum delta_1, sum delta_2}.
+__host__ __device__ inline void sure_theta(const double *sums, double sigma2, double *t0, double *t1)
+{
+    const double smm = sums[0], smd = sums[1], sdd = sums[2], sfm = sums[3], sfd = sums[4];
+    const double sd1 = sums[5], sd2 = sums[6];
+    const double b0 = sfm - sigma2 * 0.5 * (sd1 + sd2);
+    const double b1 = sfd - sigma2 * 0.5 * (sd1 - sd2);
+    double al, be;
+    solve2_sym(smm, smd, sdd, b0, b1, &al, &be);
+    *t0 = 0.5 * (al + be);
+    *t1 = 0.5 * (al - be);
+}
+
 __device__ __forceinline__ void sure_finish(const double rc[kPartials], const double cr[kPartials], double sigma2,
                                             double *info)
 {
     const double smm = cr[0], smd = cr[1], sdd = cr[2], sfm = cr[3], sfd = cr[4];
     const double sd1 = rc[5], sd2 = cr[5];
-    const double b0 = sfm - sigma2 * 0.5 * (sd1 + sd2);
-    const double b1 = sfd - sigma2 * 0.5 * (sd1 - sd2);
-    double al, be;
-    solve2_sym(smm, smd, sdd, b0, b1, &al, &be);
-    info[0] = 0.5 * (al + be);
-    info[1] = 0.5 * (al - be);
+    const double sums[7] = {smm, smd, sdd, sfm, sfd, sd1, sd2};
+    sure_theta(sums, sigma2, &info[0], &info[1]);
     info[2] = smm + 2.0 * smd + sdd;   // sum f_rc^2       (A11 of Eq. (19))
     info[3] = smm - sdd;               // sum f_rc f_cr    (A12)
     info[4] = smm - 2.0 * smd + sdd;   // sum f_cr^2       (A22)

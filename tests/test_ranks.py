@@ -141,3 +141,68 @@ def test_banded_sure_sums_all_reduce_over_two_gloo_ranks(orc):
     for o in outs:
         assert o["sums"] == pytest.approx(want, rel=1e-12)
         assert o["theta"] == pytest.approx([info["theta1"], info["theta2"]], rel=1e-9)
+
+
+SURE_BAND_GPU_CODE = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+import torch.distributed as dist
+dist.init_process_group("gloo", init_method="env://")
+from paper_1407_2343_gb300 import api, shard, synth
+rank, world = dist.get_rank(), dist.get_world_size()
+dev = torch.device("cuda:0")
+sigma, S, K = 25.0, 10, 3
+img = torch.from_numpy(synth.noisy_image(333, 270, sigma, seed=4, dtype="u8")).to(dev)
+h = api.snlm_default_h(sigma, K)
+band = shard.band_plan(img.shape[0], world, shard.reach(S, K))[rank]
+f_rc, f_cr, sums = shard.sure_band(img, band, S, K, h)      # the library's own band sums
+total = sums.cpu()
+dist.all_reduce(total)                                       # the one exchange of a banded SURE run
+theta = api.snlm_sure_theta(total.numpy(), sigma)
+out = torch.full(img.shape, float("nan"), dtype=torch.float32, device=dev)
+shard.sure_finish_band(band, f_rc, f_cr, theta, out)
+info = torch.zeros(10, dtype=torch.float64, device=dev)
+whole = api.snlm_denoise_ws(img, S, K, h, "box", "SURE", sigma, info=info)
+torch.cuda.synchronize()
+r0, r1 = band[0], band[1]
+err = float((out[r0:r1] - whole[r0:r1]).abs().max())
+dist.destroy_process_group()
+print(json.dumps({{"rank": rank, "theta": list(theta), "whole_theta": info[:2].tolist(), "err": err}}), flush=True)
+"""
+
+
+@pytest.mark.gpu
+def test_banded_sure_with_the_library_sums_over_two_gloo_ranks():
+    # two ranks (processes sharing the one GPU, each running its own independent
+    # kernels) form the seven sums of their own band with snlm_sure_band; one gloo
+    # all-reduce adds them; each solves theta and combines its rows: the result and
+    # theta are the unsharded image's
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1407_2343_gb300 import build
+
+    build.build()
+    port = _free_port()
+    code = SURE_BAND_GPU_CODE.format(root=ROOT)
+    # keep the device selection of this process (CUDA_VISIBLE_DEVICES) for both ranks
+    env = [dict(os.environ, RANK=str(r), LOCAL_RANK="0", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1",
+                MASTER_PORT=str(port)) for r in range(2)]
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env[r], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for r in range(2)]
+    outs = []
+    for p in procs:
+        try:
+            o, e = p.communicate(timeout=300)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            pytest.fail("a gloo rank did not finish")
+        assert p.returncode == 0, e[-3000:]
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    assert sorted(o["rank"] for o in outs) == [0, 1]
+    for o in outs:
+        assert o["err"] <= 1e-4
+        assert o["theta"] == pytest.approx(o["whole_theta"], abs=1e-6)
+    assert outs[0]["theta"] == outs[1]["theta"]
