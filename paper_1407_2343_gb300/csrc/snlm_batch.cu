@@ -15,176 +15,23 @@
 #include <numeric>
 
 #include "snlm_host.h"
-#include "snlm_pass_impl.cuh"
-#include "snlm_sure_impl.cuh"
+#include "snlm_batch_impl.cuh"
 
 namespace snlm {
 namespace {
 
-constexpr int kKindPass = 0, kKindSolve = 1, kKindCombine = 2;
-constexpr int kCombineChunk = 4096;      // pixels per combination unit
-constexpr int kMaxClasses = 8;           // K = 1..7 (index K)
-
-struct BatchJob {
-    PassArgs a;            // pass jobs
-    int kind;              // kKind*
-    int dm, sure;          // pass variant
-    int n_units, unit0;    // class-local queue range
-    int dep0, dep1;        // global job indices (-1: none)
-    int need0, need1;      // completion counts required from them
-    // solve
-    const double *part_rc, *part_cr;
-    int n_rc, n_cr;
-    double sigma2;
-    double *info;
-    // combination
-    const float *frc;
-    float *out;
-    long long n_px;
-};
-
-struct BatchCtl {
-    int head[kMaxClasses];  // next unit of each class
-    int err;                // a bounded wait gave up
-    int err_job;
-    int pad[6];
-};
-
-__device__ __forceinline__ int ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits (bounded) until *ctr >= need; false if the bound was hit.
-__device__ bool wait_count(const int *ctr, int need, unsigned long long limit_ns)
-{
-    if (need <= 0 || ld_acquire(ctr) >= need)
-        return true;
-    const unsigned long long t0 = global_ns();
-    while (ld_acquire(ctr) < need) {
-        if (global_ns() - t0 > limit_ns)
-            return false;
-        __nanosleep(500);
-    }
-    return true;
-}
-
-// Each pass variant is its own (not inlined) function, so that its registers are
-// allocated for it alone rather than for the union of six inlined bodies.
-template <int K, int DM, bool SURE>
-__device__ __noinline__ void pass_unit_variant(const PassArgs &a, int unit, float *smem)
-{
-    process_tile<K, DM, SURE>(a, unit, smem);
-}
-
-template <int K>
-__device__ __forceinline__ void run_pass_unit(const BatchJob &j, int unit, float *smem)
-{
-    const int sel = j.dm * 2 + j.sure;
-    switch (sel) {
-    case DIST_SLIDE * 2 + 0: pass_unit_variant<K, DIST_SLIDE, false>(j.a, unit, smem); break;
-    case DIST_SLIDE * 2 + 1: pass_unit_variant<K, DIST_SLIDE, true>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 0: pass_unit_variant<K, DIST_BLOCK, false>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 1: pass_unit_variant<K, DIST_BLOCK, true>(j.a, unit, smem); break;
-    case DIST_FIR * 2 + 0: pass_unit_variant<K, DIST_FIR, false>(j.a, unit, smem); break;
-    default: pass_unit_variant<K, DIST_FIR, true>(j.a, unit, smem); break;
-    }
-}
-
-// One persistent CTA loop over the units of one K class.
-template <int K>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
-batch_kernel(const BatchJob *__restrict__ jobs, int j0, int nj, int n_units, int cls, BatchCtl *ctl,
-             int *done, unsigned long long limit_ns)
-{
-    extern __shared__ __align__(16) float smem[];
-    __shared__ __align__(16) BatchJob sj;
-    __shared__ int s_unit, s_job, s_fail;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int u = n_units, jb = -1, fail = 0;
-            if (ld_acquire(&ctl->err) == 0) {
-                u = atomicAdd(&ctl->head[cls], 1);
-                if (u < n_units) {
-                    // job of unit u: the last job of the class with unit0 <= u
-                    int lo = j0, hi = j0 + nj - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (jobs[mid].unit0 <= u)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
-                    }
-                    jb = lo;
-                    const BatchJob &J = jobs[jb];
-                    if ((J.dep0 >= 0 && !wait_count(done + J.dep0, J.need0, limit_ns)) ||
-                        (J.dep1 >= 0 && !wait_count(done + J.dep1, J.need1, limit_ns)))
-                        fail = 1;
-                }
-            }
-            if (fail) {
-                atomicExch(&ctl->err_job, jb);
-                atomicExch(&ctl->err, 1);
-                __threadfence();
-            }
-            s_unit = u;
-            s_job = jb;
-            s_fail = fail;
-        }
-        __syncthreads();
-        const int u = s_unit;
-        if (u >= n_units || s_fail)
-            return;
-        {
-            const int *src = reinterpret_cast<const int *>(jobs + s_job);
-            int *dst = reinterpret_cast<int *>(&sj);
-            for (int i = threadIdx.x; i < (int)(sizeof(BatchJob) / sizeof(int)); i += blockDim.x)
-                dst[i] = src[i];
-        }
-        __syncthreads();
-        const int unit = u - sj.unit0;
-        if (sj.kind == kKindPass) {
-            run_pass_unit<K>(sj, unit, smem);
-        } else if (sj.kind == kKindSolve) {
-            double rc[kPartials], cr[kPartials];
-            double *sh = reinterpret_cast<double *>(smem);
-            reduce_records(sj.part_rc, sj.n_rc, sh, rc);
-            reduce_records(sj.part_cr, sj.n_cr, sh, cr);
-            if (threadIdx.x == 0)
-                sure_finish(rc, cr, sj.sigma2, sj.info);
-        } else {
-            const long long lo = (long long)unit * kCombineChunk;
-            combine_range(sj.frc, sj.out, sj.info, lo, min(sj.n_px, lo + kCombineChunk));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(done + s_job, 1);
-        }
-    }
-}
-
-using BatchFn = void (*)(const BatchJob *, int, int, int, int, BatchCtl *, int *, unsigned long long);
+using namespace snlm::batch;
 
 BatchFn batch_fn(int K)
 {
     switch (K) {
-    case 1: return batch_kernel<1>;
-    case 2: return batch_kernel<2>;
-    case 3: return batch_kernel<3>;
-    case 4: return batch_kernel<4>;
-    case 5: return batch_kernel<5>;
-    case 6: return batch_kernel<6>;
-    case 7: return batch_kernel<7>;
+    case 1: return batch_kernel_ptr<1>();
+    case 2: return batch_kernel_ptr<2>();
+    case 3: return batch_kernel_ptr<3>();
+    case 4: return batch_kernel_ptr<4>();
+    case 5: return batch_kernel_ptr<5>();
+    case 6: return batch_kernel_ptr<6>();
+    case 7: return batch_kernel_ptr<7>();
     default: return nullptr;
     }
 }

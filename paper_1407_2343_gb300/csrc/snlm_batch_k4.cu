@@ -1,0 +1,4 @@
+// Batched persistent class kernel for patch half-width K = 4.
+#include "snlm_batch_impl.cuh"
+
+SNLM_INSTANTIATE_BATCH_K(4)

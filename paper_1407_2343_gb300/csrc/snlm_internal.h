@@ -55,6 +55,7 @@ struct PassArgs {
     unsigned *check;            // checked builds: the device word a damaged guard is recorded in
     Lines aux_f;                // the noisy input image f, viewed like dst
     Lines aux_rc;               // f_rc (float32), viewed like dst: when given, the SURE sums below are formed
+    int sum_lo, sum_hi;         // only outputs in image rows [sum_lo, sum_hi) enter the sums (sum_hi == 0: all)
     // Per-CTA partial sums (SURE). With m = (f_rc + fhat)/2 and d = (f_rc - fhat)/2
     // (fhat = f_cr in the last pass of the CR order):
     //   [0] sum m^2  [1] sum m d  [2] sum d^2  [3] sum f m  [4] sum f d  [5] sum delta_out
@@ -75,6 +76,7 @@ struct DistArgs {
 struct WarpLayout {
     int LF;        // line samples (padded)
     int LW;        // one stored-weight row (SURE, padded)
+    int LK;        // SURE: the K stored-weight rows of offsets 1..K
     int LT;        // one tile-sized row (blend, SURE delta in / out, f_rc, f; padded)
     int per_warp;  // total, multiple of 4
     int guard;     // first of the kSmemGuard guard words (checked builds)
@@ -87,6 +89,7 @@ __host__ __device__ inline int pad_index(int p) { return p + p / kRun; }
 __host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool dist_only)
 {
     WarpLayout L;
+    L.LK = 0;
     const int nch = div_up(S, kRun);
     // samples at positions b0 - K + q for q < 32*kRun + nch*kRun + 2K + kRun
     const int nf = 32 * kRun + nch * kRun + 2 * K + kRun;
@@ -96,8 +99,9 @@ __host__ __device__ inline WarpLayout warp_layout(int S, int K, bool sure, bool 
     int n = L.LF;
     if (!dist_only) {
         n += L.LT;                  // the blend input of the tile
+        L.LK = sure ? K * L.LW : 0;
         if (sure)                   // stored weights for |s| <= K; delta in, delta out; f_rc and f
-            n += K * L.LW + 4 * L.LT;
+            n += L.LK + 4 * L.LT;
     }
     L.guard = n;
     L.per_warp = (n + kSmemGuard + 3) & ~3;
@@ -186,5 +190,13 @@ cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *par
 cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info, long long n,
                            cudaStream_t st);
 cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st);
+// The seven sums of a SURE band (snlm_sure_band) from the partial-sum records of the
+// last pass of each order, in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2:
+// sums = {sum m^2, sum m d, sum d^2, sum f m, sum f d, sum delta_1, sum delta_2}.
+cudaError_t launch_sure_sums(const double *part_rc, int n_rc, const double *part_cr, int n_cr, double *sums,
+                             double *scratch, cudaStream_t st);
+// out = theta1 frc + theta2 fcr over n floats (out may alias fcr).
+cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out, long long n, double theta1,
+                                 double theta2, cudaStream_t st);
 
 }  // namespace snlm

@@ -567,6 +567,7 @@ __device__ __forceinline__ void load_windows(float *smem, int per_warp, const Li
     scatter_padded(smem + w * per_warp, val, q0, len);
 }
 
+
 // 1/x for x >= 1: the SFU estimate refined by one Newton-Raphson step
 // (e = 1 - x r, r' = r + r e), which roughly squares the relative error.
 __device__ __forceinline__ float rcp_nr(float x)
@@ -704,12 +705,209 @@ struct RowOffsets {
     {
         bl = L.LF;
         wk = bl + L.LT;
-        din = wk + K * L.LW;
+        din = wk + L.LK;
         dout = din + L.LT;
         rc = dout + L.LT;
         f = rc + L.LT;
     }
 };
+
+// ---- Asynchronous load phase -------------------------------------------------
+// The common layouts load through cp.async in short rolled loops: every copy is
+// issued before the first wait, nothing is staged in registers, and the code is
+// small, so the chunk body of the search stays in the instruction cache (the
+// unrolled register gathers below cost ~15 % of a pass's issue slots in cache
+// misses alone). float32 samples are copied one by one to their padded slots from
+// reflected addresses; 8- and 16-bit samples are copied as raw aligned words into a
+// staging area (a region of the warp's rows that is idle during the load phase)
+// and converted after the wait.
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ int sample_size(int dtype) { return dtype == DT_U8 ? 1 : (dtype == DT_F16 ? 2 : 4); }
+
+// An 8- or 16-bit sample at byte offset `off` of a staging area.
+__device__ __forceinline__ float staged_sample(const unsigned char *raw, int dtype, int off)
+{
+    if (dtype == DT_U8)
+        return (float)raw[off];
+    return __half2float(*reinterpret_cast<const __half *>(raw + off));
+}
+
+// Samples [lo, hi) of row `ln` of a row-like view as words (and a ragged tail of at
+// most 3 bytes) into `stg`; returns the byte offset in the row of stg[0].
+__device__ __forceinline__ int stage_row(unsigned char *stg, const Lines &v, int ln, int lo, int hi, int lane)
+{
+    const int es = sample_size(v.dtype);
+    const unsigned char *row = static_cast<const unsigned char *>(v.ptr) + (long long)ln * v.line_step * es;
+    const int b0 = (lo * es) & ~3, b1 = hi * es, w1 = b1 & ~3;
+#pragma unroll 1
+    for (int o = b0 + 4 * lane; o < w1; o += 128)
+        cp_async4(stg + (o - b0), row + o);
+    if (w1 + lane < b1)
+        stg[w1 + lane - b0] = row[w1 + lane];
+    return b0;
+}
+
+// Positions start .. start+n-1 of the CTA's kWarpsPerCta adjacent lines of a
+// column-like view: position q's samples go to stg(q % 4) + (q / 4) * 4 * es, where
+// stg(w) = stage + w * pw floats; `reflect` maps positions through the extension.
+__device__ __forceinline__ void stage_cols(float *stage, int pw, const Lines &v, int line0, int N, int start, int n,
+                                           bool reflect)
+{
+    const int es = sample_size(v.dtype);
+    const unsigned char *base = static_cast<const unsigned char *>(v.ptr) + (long long)line0 * es;
+    const long long pstep = v.elem_step * es;
+#pragma unroll 1
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int x = reflect ? reflect_index(start + q, N) : min(start + q, N - 1);
+        unsigned char *d = reinterpret_cast<unsigned char *>(stage + (q & 3) * pw) + (q >> 2) * 4 * es;
+        if (es == 1)
+            cp_async4(d, base + x * pstep);
+        else
+            cp_async8(d, base + x * pstep);
+    }
+}
+
+// Float32 samples into padded rows: row `row` of line line0 + w holds position
+// start + q at pad_index(q), q < n; positions at or past N take `fill` (tiles) or
+// are reflected (windows).
+__device__ __forceinline__ void copy_f32(float *smem, int pw, int row, const float *img, long long ls, long long es,
+                                         int n_lines, int N, int line0, int start, int n, bool reflect, float fill)
+{
+    int w, q0;
+    gather_slot(es == 1, w, q0);
+    const int ln = line0 + w;
+    if (ln >= n_lines)
+        return;
+    const float *src = img + (long long)ln * ls;
+    float *buf = smem + w * pw + row;
+#pragma unroll 1
+    for (int q = q0; q < n; q += 32) {
+        const int x = start + q;
+        if (reflect)
+            cp_async4(buf + pad_index(q), src + (long long)reflect_index(x, N) * es);
+        else if (x < N)
+            cp_async4(buf + pad_index(q), src + (long long)x * es);
+        else
+            buf[pad_index(q)] = fill;
+    }
+}
+
+// Converts a staged view into padded float rows at `row` (windows: reflected
+// positions; tiles: zero past N).
+__device__ __forceinline__ void unstage(float *smem, int pw, int row, const float *stage, const Lines &v, int n_lines,
+                                        int N, int line0, int start, int n, int lo, bool reflect)
+{
+    const int es = sample_size(v.dtype);
+    if (v.elem_step == 1) {
+        const int w = threadIdx.x >> 5, ln = line0 + w;
+        if (ln >= n_lines)
+            return;
+        const unsigned char *stg = reinterpret_cast<const unsigned char *>(stage + w * pw);
+        const int b0 = (lo * es) & ~3;
+        float *buf = smem + w * pw + row;
+#pragma unroll 1
+        for (int q = threadIdx.x & 31; q < n; q += 32) {
+            const int x = reflect ? reflect_index(start + q, N) : start + q;
+            buf[pad_index(q)] = x < N ? staged_sample(stg, v.dtype, x * es - b0) : 0.f;
+        }
+    } else {
+        const int w = threadIdx.x % kWarpsPerCta;
+#pragma unroll 1
+        for (int q = threadIdx.x / kWarpsPerCta; q < n; q += 32) {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(stage + (q & 3) * pw) + (q >> 2) * 4 * es;
+            smem[w * pw + row + pad_index(q)] = reflect || start + q < N ? staged_sample(src, v.dtype, w * es) : 0.f;
+        }
+    }
+}
+
+// The load phase through cp.async (see above). The host launches this form only when
+// every view's layout allows it (async_layout_ok): float32 views of any layout;
+// 8- and 16-bit windows in 4-byte-aligned rows (row-like) or, column-like, in
+// aligned groups of kWarpsPerCta lines with n_lines a multiple of kWarpsPerCta; K >= 1
+// for a staged window (its staging area is the weight rows). The noisy image f of
+// the SURE sums, when it is stored in 8 or 16 bits, is gathered into registers
+// while the copies fly.
+template <bool SURE, bool STAGED>
+__device__ __forceinline__ void load_async(const PassArgs &p, float *smem, int pw, const RowOffsets &R, int line0,
+                                           int xa, int T, int ws, int len, int stage_row_off)
+{
+    const int N = p.N;
+    constexpr bool staged_win = STAGED;   // 8- or 16-bit window samples (else float32)
+    const bool gathered_f = SURE && p.aux_rc.ptr && p.aux_f.dtype != DT_F32;
+    // window samples needed: [lo, hi) covers every reflected index of [ws, ws + len)
+    int lo = 0, hi = N;
+    if (ws >= -N && ws + len <= 2 * N) {
+        lo = max(0, min(ws, 2 * N - ws - len));
+        hi = min(N, max(ws + len, -ws));
+    }
+    float *const stage = smem + stage_row_off;          // warp w's area at stage + w * pw
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ---- issue every copy
+    if constexpr (!staged_win) {
+        copy_f32(smem, pw, 0, static_cast<const float *>(p.src.ptr), p.src.line_step, p.src.elem_step, p.n_lines, N,
+                 line0, ws, len, true, 0.f);
+    } else if (p.src.elem_step == 1) {
+        if (line0 + wid < p.n_lines)
+            stage_row(reinterpret_cast<unsigned char *>(stage + wid * pw), p.src, line0 + wid, lo, hi, lane);
+    } else {
+        stage_cols(stage, pw, p.src, line0, N, ws, len, true);
+    }
+    const long long ols = p.out_line_step, oes = p.out_elem_step;
+    if (p.blend)
+        copy_f32(smem, pw, R.bl, p.blend, ols, oes, p.n_lines, N, line0, xa, T, false, 0.f);
+    if constexpr (SURE) {
+        if (p.delta_in)
+            copy_f32(smem, pw, R.din, p.delta_in, ols, oes, p.n_lines, N, line0, xa, T, false, 1.f);
+        if (p.aux_rc.ptr) {
+            copy_f32(smem, pw, R.rc, static_cast<const float *>(p.aux_rc.ptr), p.aux_rc.line_step,
+                     p.aux_rc.elem_step, p.n_lines, N, line0, xa, T, false, 0.f);
+            if (!gathered_f)
+                copy_f32(smem, pw, R.f, static_cast<const float *>(p.aux_f.ptr), p.aux_f.line_step,
+                         p.aux_f.elem_step, p.n_lines, N, line0, xa, T, false, 0.f);
+        }
+        if (!p.delta_in) {
+            int dw, dq0;
+            gather_slot(p.out_elem_step == 1, dw, dq0);
+#pragma unroll 1
+            for (int q = dq0; q < T; q += 32)
+                smem[dw * pw + R.din + pad_index(q)] = 1.f;
+        }
+    }
+    int ow, oq0;
+    gather_slot(p.out_elem_step == 1, ow, oq0);
+    const bool oline = line0 + ow < p.n_lines;
+    float vf[kTileSlots];
+    if (gathered_f && oline)
+        gather_tile_lines(vf, p.aux_f, line0 + ow, N, xa, oq0, T);
+    cp_async_wait_all();
+    if (gathered_f && oline)
+        scatter_padded(smem + ow * pw + R.f, vf, oq0, T);
+    // ---- the staged window into float rows
+    if constexpr (staged_win) {
+        __syncthreads();
+        unstage(smem, pw, 0, stage, p.src, p.n_lines, N, line0, ws, len, lo, true);
+    }
+}
+
 
 __device__ __forceinline__ void st_global_v4(float *p, float a, float b, float c, float d)
 {
@@ -755,6 +953,18 @@ __device__ __forceinline__ void unit_epilogue(const PassArgs &p, float *smem, in
     if (have_line && lane >= HR) {
         const int j = lane - HR;
         const int nvalid = min(M, qe - 8 * j);
+        // the run's outputs that enter the SURE sums: valid ones whose image row (the
+        // line of a row pass, the position of a column pass) is in [sum_lo, sum_hi)
+        int m_lo = 0, m_hi = nvalid;
+        if (SURE && p.sum_hi != 0) {
+            if (row_like) {
+                if (line < p.sum_lo || line >= p.sum_hi)
+                    m_hi = 0;
+            } else {
+                m_lo = max(0, p.sum_lo - (xa + 8 * j));
+                m_hi = min(nvalid, p.sum_hi - (xa + 8 * j));
+            }
+        }
         const float *wf_row = fl + R.wk + 9 * lane;   // w(x, s) of the lane's own positions
         const float ih2 = SURE ? __frcp_rn(p.h2) : 0.f;
         float fh[M], dv[M];
@@ -793,7 +1003,7 @@ __device__ __forceinline__ void unit_epilogue(const PassArgs &p, float *smem, in
                 const float var = A2[m] - mu * A[m];   // sum_j w (f(j) - fhat)^2
                 const float num = p.h2 + 2.f * Tt + 2.f * var;
                 dv[m] = fl[R.din + 9 * j + m] * (num * r) * ih2;
-                if (m < nvalid) {
+                if (m >= m_lo && m < m_hi) {
                     s[5] += dv[m];
                     if (p.aux_rc.ptr) {
                         // sums of the SURE system in the basis m = (f_rc + f_cr)/2, d = (f_rc - f_cr)/2
@@ -886,38 +1096,19 @@ __device__ __forceinline__ void unit_epilogue(const PassArgs &p, float *smem, in
     }
 }
 
-// One CTA-sized unit of a pass: kWarpsPerCta lines x one tile of positions.
-// `bid` enumerates the units of the pass (tile fastest). All threads of the CTA
-// must call it (it contains CTA barriers); smem must hold the pass's layout.
-template <int K, int DM, bool SURE>
-__device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *smem)
+// The load phase through register gathers (and 16-byte vector loads where the layout
+// allows): the plain passes' path, and the SURE passes' when the asynchronous copies
+// do not apply (a separate kernel instantiation, so that neither form's code or
+// registers weigh on the other).
+template <int K, bool SURE>
+__device__ __forceinline__ void load_gather(const PassArgs &p, float *smem, const WarpLayout &L, const RowOffsets &R,
+                                         int line0, int xa, int T, int b0, int nch)
 {
     constexpr int M = kRun;
-    constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
-
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int S = p.S, N = p.N;
-    const int HR = div_up(S, M), nch = div_up(S, M);
-    const int T = tile_positions(S);
-    const int tiles = p.tiles;                     // units are numbered tile fastest
-    const int grp = bid / tiles;
-    const int xa = (bid - grp * tiles) * T;
-    const int b0 = xa - HR * M;
-    const int line0 = grp * kWarpsPerCta;
     const int line = line0 + wid;
-    const WarpLayout L = warp_layout(S, K, SURE, false);
-    const RowOffsets R(L, K);
-    float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
-    if constexpr (kSmemGuard > 0) {
-        if (lane < kSmemGuard)
-            reinterpret_cast<unsigned *>(fl)[L.guard + lane] = kGuardWord ^ (unsigned)lane;
-        __syncthreads();
-    }
+    const int N = p.N;
 
-    // ---- load phase: the line windows (with reflection) and every tile input the
-    // epilogue reads. The vector forms serve the common layouts; the scalar gathers
-    // (every read issued before the first shared-memory store) serve the rest.
-    {
         const int len = 32 * M + nch * M + 2 * K + M;
         const int ws = b0 - K;
         // (the vector forms serve the plain passes: measured on GB300 they are slower
@@ -980,7 +1171,50 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
                 scatter_padded(ob + R.f, vf, oq0, T);
             }
         }
+}
+
+// One CTA-sized unit of a pass: kWarpsPerCta lines x one tile of positions.
+// `bid` enumerates the units of the pass (tile fastest). All threads of the CTA
+// must call it (it contains CTA barriers); smem must hold the pass's layout.
+// How a pass loads its inputs (a template parameter, so that each kernel holds one
+// form's code): register gathers and vector loads; asynchronous copies of a float32
+// window; asynchronous copies of an 8- or 16-bit window through the staging area.
+enum Loader { LOAD_GATHER = 0, LOAD_ASYNC_F32 = 1, LOAD_ASYNC_STAGED = 2 };
+
+template <int K, int DM, bool SURE, int LOADER = LOAD_GATHER>
+__device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *smem)
+{
+    constexpr int M = kRun;
+    constexpr int NF = M + 2 * K;        // lifted positions per run (patch halo K each side)
+
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = p.S;
+    const int HR = div_up(S, M), nch = div_up(S, M);
+    const int T = tile_positions(S);
+    const int tiles = p.tiles;                     // units are numbered tile fastest
+    const int grp = bid / tiles;
+    const int xa = (bid - grp * tiles) * T;
+    const int b0 = xa - HR * M;
+    const int line0 = grp * kWarpsPerCta;
+    const int line = line0 + wid;
+    const WarpLayout L = warp_layout(S, K, SURE, false);
+    const RowOffsets R(L, K);
+    float *const fl = smem + wid * L.per_warp;     // samples at positions b0 - K + q (padded)
+    if constexpr (kSmemGuard > 0) {
+        if (lane < kSmemGuard)
+            reinterpret_cast<unsigned *>(fl)[L.guard + lane] = kGuardWord ^ (unsigned)lane;
+        __syncthreads();
     }
+
+    // ---- load phase: the line windows (with reflection) and every tile input the
+    // epilogue reads: asynchronous copies (ASYNC, SURE passes whose layouts allow
+    // them; the staging area of 8- and 16-bit windows is the weight rows, idle until
+    // the first chunk) or register gathers and vector loads.
+    if constexpr (LOADER == LOAD_GATHER)
+        load_gather<K, SURE>(p, smem, L, R, line0, xa, T, b0, nch);
+    else
+        load_async<SURE, LOADER == LOAD_ASYNC_STAGED>(p, smem, L.per_warp, R, line0, xa, T, b0 - K,
+                                                      32 * M + nch * M + 2 * K + M, R.wk);
     __syncthreads();
 
     float fo[NF];
@@ -1021,11 +1255,11 @@ constexpr int pass_min_ctas()
     return (DM != DIST_SLIDE || K >= 6) ? 4 : 5;
 }
 
-template <int K, int DM, bool SURE>
+template <int K, int DM, bool SURE, int LOADER>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<K, DM, SURE>()) nlm_pass_kernel(const __grid_constant__ PassArgs p)
 {
     extern __shared__ __align__(16) float smem[];
-    process_tile<K, DM, SURE>(p, (int)blockIdx.x, smem);
+    process_tile<K, DM, SURE, LOADER>(p, (int)blockIdx.x, smem);
 }
 
 // Patch distances only: the same lift and reduction as the pass kernel, written
@@ -1113,12 +1347,45 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4) patch_dist_kernel(const 
     }
 }
 
-template <int K, int DM, bool SURE>
+// Whether a view of 8- or 16-bit samples can be copied as aligned 4-byte words by
+// every unit of a pass: row-like views (elem_step 1) need 4-byte-aligned rows;
+// column-like views (line_step 1) need each position's kWarpsPerCta samples aligned
+// (4 or 8 bytes) and every CTA's lines present. float32 views take any layout.
+inline bool async_view_ok(const Lines &v, int n_lines)
+{
+    if (v.dtype == DT_F32)
+        return true;
+    const long long es = v.dtype == DT_U8 ? 1 : 2;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(v.ptr);
+    if (v.elem_step == 1)
+        return (base & 3) == 0 && ((v.line_step * es) & 3) == 0;
+    if (v.line_step == 1)
+        return n_lines % kWarpsPerCta == 0 && (base & (uintptr_t)(4 * es - 1)) == 0 &&
+               ((v.elem_step * es) & (4 * es - 1)) == 0;
+    return false;
+}
+
+// The asynchronous load form of a SURE pass applies: its window's layout, and for an
+// 8- or 16-bit window a staging area (the K >= 1 weight rows) large enough.
+inline bool async_layout_ok(const PassArgs &a, int K)
+{
+    if (a.src.dtype == DT_F32)
+        return true;
+    if (K < 1 || !async_view_ok(a.src, a.n_lines))
+        return false;
+    const WarpLayout L = warp_layout(a.S, K, true, false);
+    const int len = 32 * kRun + div_up(a.S, kRun) * kRun + 2 * K + kRun;
+    const int es = a.src.dtype == DT_U8 ? 1 : 2;
+    const int bytes = a.src.elem_step == 1 ? len * es + 8 : ((len + 3) / 4) * 4 * es;
+    return ((bytes + 15) / 16) * 4 <= L.LK;
+}
+
+template <int K, int DM, bool SURE, int LOADER>
 static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
 {
     const WarpLayout L = warp_layout(a.S, K, SURE, false);
     const size_t smem = (size_t)L.per_warp * kWarpsPerCta * sizeof(float);
-    auto kern = nlm_pass_kernel<K, DM, SURE>;
+    auto kern = nlm_pass_kernel<K, DM, SURE, LOADER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -1133,13 +1400,33 @@ static cudaError_t launch_pass_t(const PassArgs &a, cudaStream_t st)
 template <int K>
 cudaError_t launch_pass(const PassArgs &a, int dist_mode, bool sure, cudaStream_t st)
 {
+    // the SURE passes load asynchronously where the layouts allow (the running-sum
+    // passes only ever read 8-bit samples, the block-sum passes 16- or 32-bit ones)
+    const int ld = !sure || !async_layout_ok(a, K) ? LOAD_GATHER
+                                                   : (a.src.dtype == DT_F32 ? LOAD_ASYNC_F32 : LOAD_ASYNC_STAGED);
     switch (dist_mode) {
     case DIST_SLIDE:
-        return sure ? launch_pass_t<K, DIST_SLIDE, true>(a, st) : launch_pass_t<K, DIST_SLIDE, false>(a, st);
+        if (!sure)
+            return launch_pass_t<K, DIST_SLIDE, false, LOAD_GATHER>(a, st);
+        if (ld == LOAD_ASYNC_STAGED)
+            return launch_pass_t<K, DIST_SLIDE, true, LOAD_ASYNC_STAGED>(a, st);
+        return launch_pass_t<K, DIST_SLIDE, true, LOAD_GATHER>(a, st);
     case DIST_BLOCK:
-        return sure ? launch_pass_t<K, DIST_BLOCK, true>(a, st) : launch_pass_t<K, DIST_BLOCK, false>(a, st);
+        if (!sure)
+            return launch_pass_t<K, DIST_BLOCK, false, LOAD_GATHER>(a, st);
+        if (ld == LOAD_ASYNC_F32)
+            return launch_pass_t<K, DIST_BLOCK, true, LOAD_ASYNC_F32>(a, st);
+        if (ld == LOAD_ASYNC_STAGED)
+            return launch_pass_t<K, DIST_BLOCK, true, LOAD_ASYNC_STAGED>(a, st);
+        return launch_pass_t<K, DIST_BLOCK, true, LOAD_GATHER>(a, st);
     default:
-        return sure ? launch_pass_t<K, DIST_FIR, true>(a, st) : launch_pass_t<K, DIST_FIR, false>(a, st);
+        if (!sure)
+            return launch_pass_t<K, DIST_FIR, false, LOAD_GATHER>(a, st);
+        if (ld == LOAD_ASYNC_F32)
+            return launch_pass_t<K, DIST_FIR, true, LOAD_ASYNC_F32>(a, st);
+        if (ld == LOAD_ASYNC_STAGED)
+            return launch_pass_t<K, DIST_FIR, true, LOAD_ASYNC_STAGED>(a, st);
+        return launch_pass_t<K, DIST_FIR, true, LOAD_GATHER>(a, st);
     }
 }
 
