@@ -788,7 +788,9 @@ __device__ __forceinline__ void stage_cols(float *stage, int pw, const Lines &v,
 
 // Float32 samples into padded rows: row `row` of line line0 + w holds position
 // start + q at pad_index(q), q < n; positions at or past N take `fill` (tiles) or
-// are reflected (windows).
+// are reflected (windows). A thread's slots are 32 positions apart, 36 floats apart
+// in the padded row; when every position lies in [0, N) the loop just walks the two
+// pointers.
 __device__ __forceinline__ void copy_f32(float *smem, int pw, int row, const float *img, long long ls, long long es,
                                          int n_lines, int N, int line0, int start, int n, bool reflect, float fill)
 {
@@ -799,6 +801,15 @@ __device__ __forceinline__ void copy_f32(float *smem, int pw, int row, const flo
         return;
     const float *src = img + (long long)ln * ls;
     float *buf = smem + w * pw + row;
+    if (start >= 0 && start + n <= N) {
+        const float *g = src + (long long)(start + q0) * es;
+        float *d = buf + pad_index(q0);
+        const long long gstep = 32 * es;
+#pragma unroll 1
+        for (int q = q0; q < n; q += 32, g += gstep, d += 36)
+            cp_async4(d, g);
+        return;
+    }
 #pragma unroll 1
     for (int q = q0; q < n; q += 32) {
         const int x = start + q;
@@ -812,11 +823,21 @@ __device__ __forceinline__ void copy_f32(float *smem, int pw, int row, const flo
 }
 
 // Converts a staged view into padded float rows at `row` (windows: reflected
-// positions; tiles: zero past N).
+// positions; tiles: zero past N). Each thread walks pointers through its slots (32
+// positions apart) when no position needs the extension.
+template <typename T>
+__device__ __forceinline__ void unstage_walk(float *d, const unsigned char *src, int step, int q, int n)
+{
+#pragma unroll 1
+    for (; q < n; q += 32, src += step, d += 36)
+        *d = to_float(*reinterpret_cast<const T *>(src));
+}
+
 __device__ __forceinline__ void unstage(float *smem, int pw, int row, const float *stage, const Lines &v, int n_lines,
                                         int N, int line0, int start, int n, int lo, bool reflect)
 {
     const int es = sample_size(v.dtype);
+    const bool inside = start >= 0 && start + n <= N;
     if (v.elem_step == 1) {
         const int w = threadIdx.x >> 5, ln = line0 + w;
         if (ln >= n_lines)
@@ -824,17 +845,37 @@ __device__ __forceinline__ void unstage(float *smem, int pw, int row, const floa
         const unsigned char *stg = reinterpret_cast<const unsigned char *>(stage + w * pw);
         const int b0 = (lo * es) & ~3;
         float *buf = smem + w * pw + row;
+        const int q0 = threadIdx.x & 31;
+        if (inside) {
+            const unsigned char *src = stg + (start + q0) * es - b0;
+            if (v.dtype == DT_U8)
+                unstage_walk<unsigned char>(buf + pad_index(q0), src, 32, q0, n);
+            else
+                unstage_walk<__half>(buf + pad_index(q0), src, 64, q0, n);
+            return;
+        }
 #pragma unroll 1
-        for (int q = threadIdx.x & 31; q < n; q += 32) {
+        for (int q = q0; q < n; q += 32) {
             const int x = reflect ? reflect_index(start + q, N) : start + q;
             buf[pad_index(q)] = x < N ? staged_sample(stg, v.dtype, x * es - b0) : 0.f;
         }
     } else {
-        const int w = threadIdx.x % kWarpsPerCta;
+        const int w = threadIdx.x % kWarpsPerCta, q0 = threadIdx.x / kWarpsPerCta;
+        if (reflect || inside) {
+            // position q's samples sit in area q % 4 at (q / 4) * 4 es; q0 % 4 stays fixed
+            const unsigned char *src =
+                reinterpret_cast<const unsigned char *>(stage + (q0 & 3) * pw) + (q0 >> 2) * 4 * es + w * es;
+            float *d = smem + w * pw + row + pad_index(q0);
+            if (v.dtype == DT_U8)
+                unstage_walk<unsigned char>(d, src, 32, q0, n);
+            else
+                unstage_walk<__half>(d, src, 64, q0, n);
+            return;
+        }
 #pragma unroll 1
-        for (int q = threadIdx.x / kWarpsPerCta; q < n; q += 32) {
+        for (int q = q0; q < n; q += 32) {
             const unsigned char *src = reinterpret_cast<const unsigned char *>(stage + (q & 3) * pw) + (q >> 2) * 4 * es;
-            smem[w * pw + row + pad_index(q)] = reflect || start + q < N ? staged_sample(src, v.dtype, w * es) : 0.f;
+            smem[w * pw + row + pad_index(q)] = start + q < N ? staged_sample(src, v.dtype, w * es) : 0.f;
         }
     }
 }
