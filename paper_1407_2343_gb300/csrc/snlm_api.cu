@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -198,9 +199,10 @@ cudaError_t run_pass(int axis, int H, int W, const Pass &ps, int S, int K, doubl
 // The four passes of Alg. 4 with the chained divergences: rows then columns into
 // frc (delta_1), columns then rows into fcr (delta_2), with the partial sums of
 // the SURE system restricted to image rows [row0, row1) (row1 == 0: all rows).
+// *n_rc and *n_cr receive the number of partial records of each order.
 cudaError_t run_sure_passes(const void *img, int dtype, int H, int W, int pitch, int S, int K, float h,
                             int profile, double bt, float *frc, float *fcr, const WsLayout &L, char *base,
-                            int row0, int row1, cudaStream_t st)
+                            int row0, int row1, cudaStream_t st, int *n_rc, int *n_cr)
 {
     float *tmp = reinterpret_cast<float *>(base + L.tmp);
     float *delta = reinterpret_cast<float *>(base + L.delta);
@@ -209,6 +211,44 @@ cudaError_t run_sure_passes(const void *img, int dtype, int H, int W, int pitch,
     const Lines tmp_rows{tmp, DT_F32, (long long)W, 1};
     const Lines tmp_cols{tmp, DT_F32, 1, (long long)W};
     cudaError_t e;
+    if (profile == SNLM_GAUSS_IIR) {
+        // The recursive profile's passes form no partial records: each keeps its
+        // chained derivative in `delta` (in place), and the sums are taken over the
+        // images after the second and the fourth pass.
+        const int r0 = row1 == 0 ? 0 : row0, r1 = row1 == 0 ? H : row1;
+        *n_rc = (int)std::min<long long>(L.n_part_rc, 1024);
+        *n_cr = (int)std::min<long long>(L.n_part_cr, 1024);
+        const Lines rows = image_lines(img, dtype, pitch, 0), cols = image_lines(img, dtype, pitch, 1);
+        {
+            TraceScope ts(SNLM_K_ROW_PASS_SURE | (DIST_IIR << 8), st);
+            if ((e = run_iir_pass_sure(rows, H, W, S, h, bt, tmp, W, 1, nullptr, delta, st)) != cudaSuccess)
+                return e;
+        }
+        {
+            TraceScope ts(SNLM_K_COL_PASS_SURE | (DIST_IIR << 8), st);
+            if ((e = run_iir_pass_sure(tmp_cols, W, H, S, h, bt, frc, 1, W, delta, delta, st)) != cudaSuccess)
+                return e;
+        }
+        {
+            TraceScope ts(SNLM_K_SURE_SOLVE, st);
+            if ((e = launch_image_sums(nullptr, nullptr, rows, W, r0, r1, delta, part_rc, *n_rc, st)) != cudaSuccess)
+                return e;
+        }
+        {
+            TraceScope ts(SNLM_K_COL_PASS_SURE | (DIST_IIR << 8), st);
+            if ((e = run_iir_pass_sure(cols, W, H, S, h, bt, tmp, 1, W, nullptr, delta, st)) != cudaSuccess)
+                return e;
+        }
+        {
+            TraceScope ts(SNLM_K_ROW_PASS_SURE | (DIST_IIR << 8), st);
+            if ((e = run_iir_pass_sure(tmp_rows, H, W, S, h, bt, fcr, W, 1, delta, delta, st)) != cudaSuccess)
+                return e;
+        }
+        TraceScope ts(SNLM_K_SURE_SOLVE, st);
+        return launch_image_sums(frc, fcr, rows, W, r0, r1, delta, part_cr, *n_cr, st);
+    }
+    *n_rc = (int)pass_ctas(W, H, S);
+    *n_cr = (int)pass_ctas(H, W, S);
     Pass p1{image_lines(img, dtype, pitch, 0), tmp};
     p1.delta_out = delta;
     if ((e = run_pass(0, H, W, p1, S, K, h, profile, bt, true, st, 0, 0)) != cudaSuccess)
@@ -281,11 +321,12 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
         SNLM_TRY(launch_set_theta(winfo, 0.5, 0.5, st));
     } else {
         // Alg. 4: rows then columns with delta_1, columns then rows with delta_2
-        SNLM_TRY(run_sure_passes(img, dtype, H, W, pitch, S, K, h, profile, bt, frc, out, L, base, 0, 0, st));
+        int n_rc = 0, n_cr = 0;
+        SNLM_TRY(run_sure_passes(img, dtype, H, W, pitch, S, K, h, profile, bt, frc, out, L, base, 0, 0, st, &n_rc,
+                                 &n_cr));
         {
             TraceScope ts(SNLM_K_SURE_SOLVE, st);
-            SNLM_TRY(launch_sure_solve(part_rc, (int)pass_ctas(W, H, S), part_cr, (int)pass_ctas(H, W, S),
-                                       (double)sigma * sigma, winfo, wsolve, st));
+            SNLM_TRY(launch_sure_solve(part_rc, n_rc, part_cr, n_cr, (double)sigma * sigma, winfo, wsolve, st));
         }
         {
             TraceScope ts(SNLM_K_COMBINE, st);
@@ -384,13 +425,14 @@ int snlm_sure_band(const void *img, int dtype, int H, int W, int pitch, int S, i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(workspace);
     const double bt = beta_or_default(beta, K);
+    int n_rc = 0, n_cr = 0;
     cudaError_t e = run_sure_passes(img, dtype, H, W, pitch, S, K, h, profile, bt, f_rc, f_cr, L, base, row0, row1,
-                                    st);
+                                    st, &n_rc, &n_cr);
     if (e != cudaSuccess)
         return status_of(e);
     TraceScope ts(SNLM_K_SURE_SOLVE, st);
-    e = launch_sure_sums(reinterpret_cast<double *>(base + L.part_rc), (int)pass_ctas(W, H, S),
-                         reinterpret_cast<double *>(base + L.part_cr), (int)pass_ctas(H, W, S), sums,
+    e = launch_sure_sums(reinterpret_cast<double *>(base + L.part_rc), n_rc,
+                         reinterpret_cast<double *>(base + L.part_cr), n_cr, sums,
                          reinterpret_cast<double *>(base + L.solve), st);
     return status_of(e);
 }
@@ -836,8 +878,8 @@ const char *snlm_kernel_name(int kind)
     static const char *names[14][5] = {
         {"row_pass", "row_pass/slide", "row_pass/block", "row_pass/fir", "row_pass/iir"},
         {"col_pass", "col_pass/slide", "col_pass/block", "col_pass/fir", "col_pass/iir"},
-        {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir", "unknown"},
-        {"col_pass_sure", "col_pass_sure/slide", "col_pass_sure/block", "col_pass_sure/fir", "unknown"},
+        {"row_pass_sure", "row_pass_sure/slide", "row_pass_sure/block", "row_pass_sure/fir", "row_pass_sure/iir"},
+        {"col_pass_sure", "col_pass_sure/slide", "col_pass_sure/block", "col_pass_sure/fir", "col_pass_sure/iir"},
         {"sure_solve", "sure_solve", "sure_solve", "sure_solve", "sure_solve"},
         {"combine", "combine", "combine", "combine", "combine"},
         {"set_theta", "set_theta", "set_theta", "set_theta", "set_theta"},

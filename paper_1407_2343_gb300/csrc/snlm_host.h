@@ -108,8 +108,6 @@ inline int check_denoise(int H, int W, int S, int K, float h, int profile, int o
     const int rc = check_common(H, W, S, K, h, SNLM_GAUSS, order, sigma);
     if (rc != SNLM_OK)
         return rc;
-    if (order == SNLM_SURE)
-        return SNLM_ERR_UNSUPPORTED;
     return iir_check_beta(beta_or_default(beta, K));
 }
 

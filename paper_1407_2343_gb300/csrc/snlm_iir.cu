@@ -41,6 +41,8 @@
 
 #include <cuda_fp16.h>
 
+#include <vector>
+
 namespace snlm {
 
 namespace {
@@ -71,7 +73,15 @@ struct IirArgs {
     long long out_line_step, out_elem_step;
     const float *blend;          // optional: dst = (fhat + blend) / 2, indexed like dst
     float *dist;                 // ... or the distances (n_lines, N, 2S+1), float32
+    // divergence of Eq. (24) (SURE passes): the profile's weight at each lag, its
+    // centre weight and h^2; delta in (NULL = 1) and out, indexed like dst
+    float geff[kMaxS + 1];
+    float g0, h2;
+    const float *delta_in;
+    float *delta_out;
 };
+
+constexpr int kIirPass = 0, kIirDist = 1, kIirSure = 2;   // what iir_pass_kernel computes
 
 // Half-sample symmetric extension of any x onto [0, n).
 __device__ __forceinline__ int iir_reflect(int x, int n)
@@ -235,11 +245,18 @@ __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float
     }
 }
 
-// DIST = false: the 1-D NLM pass of Eq. (4) with the recursive profile.
-// DIST = true: the distances d^2(x, x+s), s in [-S, S], written to a.dist.
-template <bool DIST>
-__global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirArgs a)
+// MODE kIirPass: the 1-D NLM pass of Eq. (4) with the recursive profile.
+// MODE kIirDist: the distances d^2(x, x+s), s in [-S, S], written to a.dist.
+// MODE kIirSure: the pass and the divergence of Eq. (24) with the profile's weight at
+// each lag (reading R17): per pixel x and offset s the patch term takes
+// w(x, s) g(s) (a_s - mu) a_-s + w(x-s, s) g(s) (a_-s - mu) a_s, a_s = f(x+s) - f(x),
+// kept as TA - mu TB; the owner of x reads f(x-s) from the window row and w(x-s, s)
+// from the pushed weights. Three more accumulators per position: one CTA per SM.
+template <int MODE>
+__global__ void __launch_bounds__(kIirWarps * 32, MODE == kIirSure ? 1 : 2) iir_pass_kernel(const IirArgs a)
 {
+    constexpr bool DIST = MODE == kIirDist;
+    constexpr bool SURE = MODE == kIirSure;
     extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *fs = smem + warp * (DIST ? 1 : 3) * kIirRow;  // f(b0 + q), q < kIirSpan + S
@@ -258,11 +275,14 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
         iir_gather(fs, a.src, ln, a.N, b0, lane, nf);
         __syncwarp();
         float fo[kIirRun], accA[kIirRun], accQ[kIirRun];
+        float accA2[SURE ? kIirRun : 1], accTA[SURE ? kIirRun : 1], accTB[SURE ? kIirRun : 1];
 #pragma unroll
         for (int m = 0; m < kIirRun; ++m) {
             fo[m] = fs[iir_pad(base + m)];
             accA[m] = 0.f;
             accQ[m] = 0.f;
+            if constexpr (SURE)
+                accA2[m] = accTA[m] = accTB[m] = 0.f;
         }
         for (int s = 1; s <= a.S; ++s) {
             float dl[kIirRun], y[kIirRun];
@@ -284,6 +304,8 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
                         a.dist[(row + x + s) * stride + a.S - s] = d;      // d^2(x+s, x)
                 }
             } else {
+                float am[SURE ? kIirRun : 1];            // SURE: a_-s = f(x-s) - f(x)
+                const float gs = SURE ? a.geff[s] : 0.f;
 #pragma unroll
                 for (int m = 0; m < kIirRun; ++m) {
                     // the filter's response is non-negative, so a negative output is
@@ -294,6 +316,15 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
                     accQ[m] += wt;
                     pw[iir_pad(ib + m)] = wt;            // the pair's share of pixel x + s
                     pd[iir_pad(ib + m)] = wd;
+                    if constexpr (SURE) {
+                        // positions below s (only before the tile's first output) read a
+                        // clamped, unused sample
+                        am[m] = fs[iir_pad(max(base + m - s, 0))] - fo[m];
+                        const float wg = gs * wt;
+                        accA2[m] = fmaf(wd, dl[m], accA2[m]);
+                        accTA[m] = fmaf(wg, dl[m] * am[m], accTA[m]);
+                        accTB[m] = fmaf(wg, am[m], accTB[m]);
+                    }
                 }
                 __syncwarp();
                 // every position q >= s received the push of q - s, whose difference
@@ -301,8 +332,17 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
                 // tile's first output
 #pragma unroll
                 for (int m = 0; m < kIirRun; ++m) {
-                    accA[m] -= pd[iir_pad(base + m)];
-                    accQ[m] += pw[iir_pad(base + m)];
+                    const float db = pd[iir_pad(base + m)], wb = pw[iir_pad(base + m)];
+                    accA[m] -= db;
+                    accQ[m] += wb;
+                    if constexpr (SURE) {
+                        // the pair (x-s, x): weight wb, difference f(x-s) - f(x) = a_-s, and
+                        // db = wb (f(x) - f(x-s)), so wb a_-s^2 = -db a_-s
+                        const float wg = gs * wb;
+                        accA2[m] = fmaf(-db, am[m], accA2[m]);
+                        accTA[m] = fmaf(wg, dl[m] * am[m], accTA[m]);
+                        accTB[m] = fmaf(wg, dl[m], accTB[m]);
+                    }
                 }
                 __syncwarp();
             }
@@ -315,11 +355,23 @@ __global__ void __launch_bounds__(kIirWarps * 32, 2) iir_pass_kernel(const IirAr
             if constexpr (DIST) {
                 a.dist[((long long)ln * a.N + x) * (2 * a.S + 1) + a.S] = 0.f;
             } else {
-                float v = fo[m] + accA[m] / (1.f + accQ[m]);
+                const float Wt = 1.f + accQ[m];
+                const float mu = accA[m] / Wt;
+                float v = fo[m] + mu;
                 const long long o = (long long)ln * a.out_line_step + (long long)x * a.out_elem_step;
                 if (a.blend)
                     v = 0.5f * (v + a.blend[o]);
                 a.dst[o] = v;
+                if constexpr (SURE) {
+                    // Eq. (24) with the profile's centre weight g0 (reading R17):
+                    // delta_out = delta_in (h^2 + 2 g0 var + 2 T) / (W h^2),
+                    // var = sum_j w (f(j) - fhat)^2 = A2 - mu A, T = TA - mu TB
+                    const float var = fmaf(-mu, accA[m], accA2[m]);
+                    const float T = fmaf(-mu, accTB[m], accTA[m]);
+                    const float num = fmaf(2.f * a.g0, var, fmaf(2.f, T, a.h2));
+                    const float din = a.delta_in ? a.delta_in[o] : 1.f;
+                    a.delta_out[o] = din * num / (Wt * a.h2);
+                }
             }
         }
     }
@@ -408,23 +460,48 @@ int iir_plan(double beta, int S, IirArgs &a)
     return SNLM_OK;
 }
 
-cudaError_t launch_iir(const IirArgs &a, bool dist, cudaStream_t st)
+template <int MODE>
+cudaError_t launch_iir_t(const IirArgs &a, dim3 grid, int smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(iir_pass_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        iir_pass_kernel<MODE><<<grid, kIirWarps * 32, smem, st>>>(a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_iir(const IirArgs &a, int mode, cudaStream_t st)
 {
     const int tiles = div_up(a.N, a.T);
     const int groups = div_up(a.n_lines, kIirWarps);
     const dim3 grid((unsigned)tiles, (unsigned)(groups < 65535 ? groups : 65535));
+    const bool dist = mode == kIirDist;
     const int smem = kIirWarps * (dist ? 1 : 3) * kIirRow * (int)sizeof(float);   // 66 KB (pass), 22 KB
-    cudaError_t e;
-    if (dist) {
-        e = cudaFuncSetAttribute(iir_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            iir_pass_kernel<true><<<grid, kIirWarps * 32, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(iir_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            iir_pass_kernel<false><<<grid, kIirWarps * 32, smem, st>>>(a);
+    if (mode == kIirDist)
+        return launch_iir_t<kIirDist>(a, grid, smem, st);
+    if (mode == kIirSure)
+        return launch_iir_t<kIirSure>(a, grid, smem, st);
+    return launch_iir_t<kIirPass>(a, grid, smem, st);
+}
+
+// The profile's weight at the lags 0..S: beta sqrt(2 pi) times the two-pass impulse
+// response (the weight of the lifted square at x + s in d^2(x, .)), from the same
+// recursion run in double on a unit impulse far from both ends.
+void iir_lag_weights(double beta, int S, float *geff)
+{
+    const IirDesign d = iir_design(beta);
+    const int L = 4096 + S, n = 2 * L + 1;
+    std::vector<double> w((size_t)n, 0.0), y((size_t)n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double x = i == L ? d.B : 0.0;
+        w[i] = x + (i >= 1 ? d.a[0] * w[i - 1] : 0.0) + (i >= 2 ? d.a[1] * w[i - 2] : 0.0) +
+               (i >= 3 ? d.a[2] * w[i - 3] : 0.0);
     }
-    return e != cudaSuccess ? e : cudaGetLastError();
+    for (int i = n - 1; i >= 0; --i)
+        y[i] = d.B * w[i] + (i + 1 < n ? d.a[0] * y[i + 1] : 0.0) + (i + 2 < n ? d.a[1] * y[i + 2] : 0.0) +
+               (i + 3 < n ? d.a[2] * y[i + 3] : 0.0);
+    const double scale = beta * sqrt(2.0 * 3.14159265358979323846);
+    for (int s = 0; s <= S; ++s)
+        geff[s] = (float)(scale * y[L + s]);
 }
 
 }  // namespace
@@ -455,7 +532,35 @@ cudaError_t run_iir_pass(const Lines &src, int n_lines, int N, int S, double h, 
     a.out_line_step = out_line_step;
     a.out_elem_step = out_elem_step;
     a.blend = blend;
-    return launch_iir(a, false, st);
+    return launch_iir(a, kIirPass, st);
+}
+
+cudaError_t run_iir_pass_sure(const Lines &src, int n_lines, int N, int S, double h, double beta, float *dst,
+                              long long out_line_step, long long out_elem_step, const float *delta_in,
+                              float *delta_out, cudaStream_t st)
+{
+    IirArgs a;
+    memset(&a, 0, sizeof(a));
+    if (S > kMaxS || iir_plan(beta, S, a) != SNLM_OK)
+        return cudaErrorInvalidValue;
+    a.src = src;
+    a.n_lines = n_lines;
+    a.N = N;
+    a.S = S;
+    const IirDesign d = iir_design(beta);
+    double c = -1.4426950408889634 * beta * sqrt(2.0 * 3.14159265358979323846) * d.B * d.B / (h * h);
+    if (!(c > -3.0e38))
+        c = -3.0e38;
+    a.c2 = (float)c;
+    a.dst = dst;
+    a.out_line_step = out_line_step;
+    a.out_elem_step = out_elem_step;
+    iir_lag_weights(beta, S, a.geff);
+    a.g0 = a.geff[0];
+    a.h2 = (float)(h * h);
+    a.delta_in = delta_in;
+    a.delta_out = delta_out;
+    return launch_iir(a, kIirSure, st);
 }
 
 cudaError_t run_iir_dist(const Lines &src, int n_lines, int N, int S, double beta, float *out, cudaStream_t st)
@@ -469,7 +574,7 @@ cudaError_t run_iir_dist(const Lines &src, int n_lines, int N, int S, double bet
     a.N = N;
     a.S = S;
     a.dist = out;
-    return launch_iir(a, true, st);
+    return launch_iir(a, kIirDist, st);
 }
 
 }  // namespace snlm

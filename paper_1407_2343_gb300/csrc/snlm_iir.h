@@ -25,5 +25,11 @@ int iir_check_beta(double beta);
 cudaError_t run_iir_pass(const Lines &src, int n_lines, int N, int S, double h, double beta, float *dst,
                          long long out_line_step, long long out_elem_step, const float *blend, cudaStream_t st);
 cudaError_t run_iir_dist(const Lines &src, int n_lines, int N, int S, double beta, float *out, cudaStream_t st);
+// run_iir_pass_sure: the pass with the divergence of Eq. (24) for the recursive
+// profile (reading R17): delta_out = delta_in (NULL = 1) times the derivative of the
+// pass, both indexed like dst (delta_in may alias delta_out).
+cudaError_t run_iir_pass_sure(const Lines &src, int n_lines, int N, int S, double h, double beta, float *dst,
+                              long long out_line_step, long long out_elem_step, const float *delta_in,
+                              float *delta_out, cudaStream_t st);
 
 }  // namespace snlm

@@ -195,6 +195,10 @@ cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st
 // sums = {sum m^2, sum m d, sum d^2, sum f m, sum f d, sum delta_1, sum delta_2}.
 cudaError_t launch_sure_sums(const double *part_rc, int n_rc, const double *part_cr, int n_cr, double *sums,
                              double *scratch, cudaStream_t st);
+// Records of the SURE sums over rows [r0, r1) of dense W-wide images (frc == NULL:
+// the delta sum only), n_records blocks: for the passes without records of their own.
+cudaError_t launch_image_sums(const float *frc, const float *fcr, const Lines &f, int W, int r0, int r1,
+                              const float *delta, double *records, int n_records, cudaStream_t st);
 // out = theta1 frc + theta2 fcr over n floats (out may alias fcr).
 cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out, long long n, double theta1,
                                  double theta2, cudaStream_t st);

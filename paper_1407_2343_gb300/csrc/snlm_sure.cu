@@ -2,6 +2,8 @@
 // reduce the per-CTA partial sums of the last pass of each order, solve the 2x2
 // system A theta = b of Eqs. (19) and (25), and form theta1 f_rc + theta2 f_cr
 // (Eq. (14)).
+#include <cuda_fp16.h>
+
 #include "snlm_internal.h"
 #include "snlm_sure_impl.cuh"
 
@@ -102,6 +104,51 @@ __global__ void combine_theta_kernel(const float *__restrict__ frc, const float 
     }
 }
 
+// Partial records of the SURE sums over whole images, for the passes that form no
+// records of their own (the recursive profile's): block b takes the pixels of rows
+// [r0, r1) at flat indices b*256 + t, + gridDim.x*256, ..., forms in float32
+//   m = (frc + fcr)/2, d = (frc - fcr)/2:  m^2, m d, d^2, f m, f d, delta
+// (frc == NULL: delta only), accumulates them per thread in FP64 and reduces the
+// block in a fixed tree into record b (kPartials doubles, the unused ones zero).
+__global__ void __launch_bounds__(kSolveThreads) image_sums_kernel(const float *__restrict__ frc,
+                                                                   const float *__restrict__ fcr, Lines f, int W,
+                                                                   int r0, int r1, const float *__restrict__ delta,
+                                                                   double *records)
+{
+    __shared__ double sh[kPartials * kSolveThreads];
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long lo = (long long)r0 * W, hi = (long long)r1 * W;
+    for (long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+         i += (long long)gridDim.x * blockDim.x) {
+        acc[5] += (double)delta[i];
+        if (frc) {
+            const int r = (int)(i / W), c = (int)(i - (long long)r * W);
+            const float a = frc[i], b = fcr[i];
+            const float m = 0.5f * (a + b), d = 0.5f * (a - b);
+            const long long fo = (long long)r * f.line_step + c;
+            const float fv = f.dtype == DT_U8 ? (float)static_cast<const unsigned char *>(f.ptr)[fo]
+                             : f.dtype == DT_F16 ? __half2float(static_cast<const __half *>(f.ptr)[fo])
+                                                 : static_cast<const float *>(f.ptr)[fo];
+            acc[0] += (double)(m * m);
+            acc[1] += (double)(m * d);
+            acc[2] += (double)(d * d);
+            acc[3] += (double)(fv * m);
+            acc[4] += (double)(fv * d);
+        }
+    }
+    for (int k = 0; k < kPartials; ++k)
+        sh[k * kSolveThreads + threadIdx.x] = k < 6 ? acc[k] : 0.0;
+    __syncthreads();
+    for (int stride = kSolveThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride)
+            for (int k = 0; k < kPartials; ++k)
+                sh[k * kSolveThreads + threadIdx.x] += sh[k * kSolveThreads + threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x < kPartials)
+        records[(long long)blockIdx.x * kPartials + threadIdx.x] = sh[threadIdx.x * kSolveThreads];
+}
+
 __global__ void set_theta_kernel(double *info, double t0, double t1)
 {
     if (threadIdx.x < 10)
@@ -174,6 +221,13 @@ cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out,
     if (blocks > (long long)sms * 8)
         blocks = (long long)sms * 8;
     combine_theta_kernel<<<(unsigned)blocks, 256, 0, st>>>(frc, fcr, out, n, theta1, theta2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_sums(const float *frc, const float *fcr, const Lines &f, int W, int r0, int r1,
+                              const float *delta, double *records, int n_records, cudaStream_t st)
+{
+    image_sums_kernel<<<n_records, kSolveThreads, 0, st>>>(frc, fcr, f, W, r0, r1, delta, records);
     return cudaGetLastError();
 }
 

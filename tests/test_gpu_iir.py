@@ -102,7 +102,7 @@ def test_nlm_1d_strided_columns(dev, api, orc):
     assert np.abs(np_of(out) - ref).max() <= TOL
 
 
-@pytest.mark.parametrize("order", ["RC", "CR", "AVG"])
+@pytest.mark.parametrize("order", ["RC", "CR", "AVG", "SURE"])
 @pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
 def test_denoise_256(dev, api, orc, order, dtype):
     # the 256x256 scene of the small configuration (sigma = 20, S = 10) with the
@@ -110,9 +110,52 @@ def test_denoise_256(dev, api, orc, order, dtype):
     sigma, S, K, beta = 20.0, 10, 3, 1.5
     img = synth.noisy_image(256, 256, sigma, seed=0, dtype=dtype)
     h = orc.default_h(sigma, K, "gauss_iir", beta)
-    ref, _ = orc.snlm(img.astype(np.float64), S, K, h, "gauss_iir", beta, order=order)
-    got = np_of(api.snlm_denoise(to_dev(img, dev), S, K, h, "gauss_iir", order, 0.0, beta))
+    ref, _ = orc.snlm(img.astype(np.float64), S, K, h, "gauss_iir", beta, order=order, sigma=sigma)
+    got = np_of(api.snlm_denoise(to_dev(img, dev), S, K, h, "gauss_iir", order, sigma, beta))
     assert np.abs(got - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("sigma,S,K,dtype", [(10.0, 10, 2, "f32"), (20.0, 10, 3, "u8"), (30.0, 10, 5, "f16"),
+                                             (50.0, 20, 7, "u8"), (25.0, 0, 3, "f32")])
+def test_sure_order_theta_and_sums(dev, api, orc, sigma, S, K, dtype):
+    # Alg. 4 in the SURE order with the recursive profile: the divergence of Eq. (24)
+    # with the profile's centre weight and its patch term over the whole window
+    # (reading R17), theta of Eqs. (19), (25) and the seven sums against the oracle
+    import torch
+
+    beta = K / 2.0
+    img = synth.noisy_image(200, 230, sigma, seed=int(sigma) + S + K, dtype=dtype)
+    h = orc.default_h(sigma, K, "gauss_iir", beta)
+    ref, ri = orc.snlm(img.astype(np.float64), S, K, h, "gauss_iir", beta, order="SURE", sigma=sigma)
+    info = torch.zeros(10, dtype=torch.float64, device=dev)
+    got = np_of(api.snlm_denoise_ws(to_dev(img, dev), S, K, h, "gauss_iir", "SURE", sigma, beta, info=info))
+    gi = np_of(info)
+    assert np.abs(got - ref).max() <= TOL
+    assert abs(gi[0] - ri["theta1"]) <= 1e-5 and abs(gi[1] - ri["theta2"]) <= 1e-5, (gi[:2], ri)
+    for k, name in enumerate(["A11", "A12", "A22", "sum_f_frc", "sum_f_fcr"]):
+        assert gi[2 + k] == pytest.approx(ri[name], rel=1e-5), name
+    for k, name in ((7, "sum_d1"), (8, "sum_d2")):
+        assert gi[k] == pytest.approx(ri[name], rel=1e-4, abs=1e-2), name
+
+
+def test_sure_order_in_row_bands(dev, api, orc):
+    # the banded SURE exchange with the recursive profile: bands widened by its reach
+    import torch
+
+    from paper_1407_2343_gb300 import shard
+
+    sigma, S, K, beta = 25.0, 10, 5, 2.5
+    img = synth.noisy_image(300, 180, sigma, seed=3, dtype="u8")
+    h = orc.default_h(sigma, K, "gauss_iir", beta)
+    t = to_dev(img, dev)
+    whole = api.snlm_denoise(t, S, K, h, "gauss_iir", "SURE", sigma, beta)
+    ref, ri = orc.snlm(img.astype(np.float64), S, K, h, "gauss_iir", beta, order="SURE", sigma=sigma)
+    for n in (2, 3):
+        banded, theta = shard.denoise_bands(t, S, K, h, "gauss_iir", "SURE", beta, n_bands=n, sigma=sigma)
+        torch.cuda.synchronize()
+        assert float((banded - whole).abs().max()) <= TOL
+        assert np.abs(np_of(banded) - ref).max() <= TOL
+        assert abs(theta[0] - ri["theta1"]) <= 1e-5 and abs(theta[1] - ri["theta2"]) <= 1e-5
 
 
 @pytest.mark.parametrize("sigma", [10.0, 20.0, 30.0, 50.0])
@@ -160,8 +203,6 @@ def test_unsupported_and_invalid_requests(dev, api):
     img = torch.zeros((16, 16), dtype=torch.uint8, device=dev)
     out = torch.full((16, 16), 7.0, device=dev)
     p = lambda t: t.data_ptr()  # noqa: E731
-    # SURE needs the divergence of Eq. (24), which is not formed for this profile
-    assert lib.snlm_denoise(p(img), 0, 16, 16, 16, 5, 3, 10.0, 2, 3, 5.0, 1.5, p(out), None) == api.ERR_UNSUPPORTED
     # beta outside [0.5, 3.5]
     assert lib.snlm_denoise(p(img), 0, 16, 16, 16, 5, 3, 10.0, 2, 0, 0.0, 0.4, p(out), None) == api.ERR_ARG
     assert lib.snlm_denoise(p(img), 0, 16, 16, 16, 5, 3, 10.0, 2, 0, 0.0, 3.6, p(out), None) == api.ERR_ARG
