@@ -372,11 +372,12 @@ def measure_3d(a, api, dev, stream, flush):
 
 def measure_iir(a, api, dev, stream, flush):
     """The recursive Gaussian profile (Sec. II-B) against the exact (2K+1)-tap
-    Gaussian of Eq. (3) on the benchmark's scene, AVG order (four passes, like
-    SURE, which this profile does not run): device time per call (from the
+    Gaussian of Eq. (3) on the benchmark's scene, AVG order (four passes): device
+    time per call (from the
     library's launch trace, L2 flushed between calls) at beta = K/2 for K = 2, 5
     and 7, the roofline of the dominant recursive pass, and each output's PSNR
-    against the clean scene with their mean difference."""
+    against the clean scene with their mean difference; then the SURE order of both
+    profiles at K = 5 (CUDA events per call)."""
     import torch
     from paper_1407_2343_gb300 import synth
 
@@ -424,6 +425,25 @@ def measure_iir(a, api, dev, stream, flush):
             case[prof] = c
         case["mean_abs_diff"] = float((outs["gauss_iir"] - outs["gauss"]).abs().mean())
         res["cases"].append(case)
+    # the SURE order (all of Alg. 4, with the divergence of Eq. (24)) at K = 5, beta = 2.5
+    ws_s = torch.empty(api.snlm_workspace_bytes(a.size, a.size, "SURE"), dtype=torch.uint8, device=dev)
+    sure = {"K": 5, "beta": 2.5}
+    for prof in ("gauss_iir", "gauss"):
+        h = api.snlm_default_h(a.sigma, 5, prof, 2.5)
+        for _ in range(2):
+            api.snlm_denoise_ws(img, a.S, 5, h, prof, "SURE", a.sigma, 2.5, out=out, workspace=ws_s, stream=stream)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            api.snlm_denoise_ws(img, a.S, 5, h, prof, "SURE", a.sigma, 2.5, out=out, workspace=ws_s, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+        sure[prof] = {"ms": ms, "Mpixel_s": px / (ms * 1e-3) / 1e6,
+                      "psnr_db": float(10 * math.log10(255.0 ** 2 / float(((out - clean) ** 2).mean())))}
+    res["sure_order"] = sure
     return res
 
 
@@ -605,7 +625,7 @@ def measure_served(a, dev):
     import torch
 
     import oracle
-    from paper_1407_2343_gb300 import serve
+    from paper_1407_2343_gb300 import api, serve
 
     n, reps = a.serve_requests, a.serve_repeats
     pool = serve.make_pool()
@@ -621,8 +641,21 @@ def measure_served(a, dev):
         return sched
 
     plain_srv, served_srv = serve.NativeServer("plain"), serve.NativeServer("batched")
-    # warm-up of both loops (module loading and kernel attributes of every variant)
+    # warm-up of both loops: every kernel variant a schedule can reach is loaded and
+    # configured once (each combination of S, K, profile, order and storage, on the
+    # batched path at 128^2 and on the per-image path at 1024^2), then a random mix
+    warm = []
+    for sz in (128, 1024):
+        for S in (5, 10, 15, 20):
+            for K in (2, 3, 5):
+                for prof in ("box", "gauss"):
+                    for order in ("RC", "CR", "AVG", "SURE"):
+                        for k in (0, 1):
+                            img, sigma = pool[(sz, k)]
+                            h = api.snlm_default_h(sigma, K, prof, K / 2.0)
+                            warm.append(serve.Request(len(warm), img, S, K, h, prof, order, sigma, K / 2.0, 0.0))
     for srv in (plain_srv, served_srv):
+        srv.run(serve.prepare_outputs(warm))
         srv.run(schedule(1e9, 4, min(n, 400)))
     # capacity of the plain path: everything arrives at once (best of two runs)
     cap = 0.0

@@ -358,7 +358,11 @@ bool start_launches(snlm_server *s, int *err)
     while (!s->queue.empty()) {
         const int front = s->queue.front();
         const snlm_serve_request &fr = s->reqs[front].r;
-        const int si = free_stream(s, pixels(fr) < s->cfg.solo_pixels);
+        // small launches take the high-priority streams; so does a large one that
+        // starts on an idle GPU, so that requests arriving after it do not preempt it
+        // (at low load that is what keeps the large requests' latency at the plain
+        // path's); a large launch that joins running work yields to later small ones
+        const int si = free_stream(s, pixels(fr) < s->cfg.solo_pixels || s->inflight.empty());
         if (si < 0 || (plain && !s->inflight.empty()))
             break;
         Launch L;
@@ -562,19 +566,12 @@ int snlm_server_drain(snlm_server *s)
         if (err != SNLM_OK)
             break;
         if (!progress) {
-            // Nothing to do until an arrival or a completion. With work in flight or
-            // queued, poll again after yielding the core: a timed sleep can overshoot
-            // by milliseconds on a loaded host, far longer than a launch takes. With
-            // the GPU idle and the queue empty, sleep until shortly before the next
-            // arrival, then poll.
+            // Nothing to do until an arrival or a completion: poll again after yielding
+            // the core. The loop never sleeps: a timed sleep overshot by up to ~10 ms on
+            // the shared host, which over a 2000-request schedule set the p99 of the
+            // lightly loaded points (17 ms at 0.2x of capacity).
             const auto w0 = std::chrono::steady_clock::now();
-            double until = 0.0;
-            if (s->queue.empty() && s->inflight.empty() && s->next < s->order.size())
-                until = s->reqs[s->order[s->next]].r.t_arrival - s->clock();
-            if (until > 300e-6)
-                std::this_thread::sleep_for(std::chrono::duration<double>(std::min(2e-3, until - 200e-6)));
-            else
-                std::this_thread::yield();
+            std::this_thread::yield();
             idle += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
         }
     }
