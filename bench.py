@@ -49,12 +49,13 @@ OPS_PER_PAIR_IIR = 15
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # pass kernels of the 4096^2 u8 SURE step, from one ncu --set full capture of
 # `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
-# --no-cpu-baseline --no-rc --no-bf --no-nlm2d` (the first timed step's four
-# passes); valid only while the pass kernels' sources (PASS_KERNEL_SOURCES) hash to
-# `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "b3a4cc4c39b91cf4",
-           "bytes_per_launch": {"row_pass_sure/slide": 91099136, "col_pass_sure/block": 179085824,
-                                "col_pass_sure/slide": 96861696, "row_pass_sure/block": 267706880}}
+# --no-cpu-baseline --no-rc --no-bf --no-nlm2d --no-3d --no-iir --no-fp16
+# --no-precision` (the first timed step's four passes); valid only while the
+# pass kernels' sources (PASS_KERNEL_SOURCES) hash to `sources_sha` (profiles/ has
+# the capture's summary).
+TRAFFIC = {"sources_sha": "f6ed7b21fb79dc29",
+           "bytes_per_launch": {"row_pass_sure/slide": 90699776, "col_pass_sure/block": 179043840,
+                                "col_pass_sure/slide": 96404480, "row_pass_sure/block": 268333056}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -675,6 +676,12 @@ def measure_served(a, dev):
                 v = [r[key] for r in runs[mode]]
                 agg[key] = float(np.median(v))
                 agg[key + "_range"] = [float(min(v)), float(max(v))]
+            sizes = sorted({k for r in runs[mode] for k in r["by_size"]}, key=int)
+            agg["p99_ms_by_size"] = {k: float(np.median([r["by_size"][k]["p99_ms"] for r in runs[mode]
+                                                         if k in r["by_size"]])) for k in sizes}
+            agg["loop_max_yield_ms"] = max(r["loop"].get("max_yield_ms", 0.0) for r in runs[mode])
+            agg["loop_max_iter_ms"] = max(r["loop"].get("max_iter_ms", 0.0) for r in runs[mode])
+            agg["loop_yields_over_1ms"] = sum(r["loop"].get("yields_over_1ms", 0) for r in runs[mode])
             agg["max_batch"] = max(r["max_batch"] for r in runs[mode])
             agg["max_inflight_steps"] = max(r["max_inflight_steps"] for r in runs[mode])
             pt[mode] = agg

@@ -459,6 +459,9 @@ typedef struct {
     long long budget_bytes;   /* the slab */
     double wall_s;            /* server clock at the end of the last drain */
     double host_busy_s;       /* time the loop spent not sleeping */
+    double max_yield_s;       /* longest single yield of the core while idle (host scheduling) */
+    double max_iter_s;        /* longest pass of the loop's own work (admission, launch, retire) */
+    int yields_over_1ms;      /* yields that kept the loop away for more than 1 ms */
 } snlm_server_stats;
 
 typedef struct snlm_server snlm_server;

@@ -54,7 +54,8 @@ class ServerStats(ctypes.Structure):
     """snlm_server_stats of include/snlm.h."""
     _fields_ = [("launches", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_inflight", ctypes.c_int),
                 ("images", ctypes.c_int), ("max_used_bytes", ctypes.c_longlong),
-                ("budget_bytes", ctypes.c_longlong), ("wall_s", ctypes.c_double), ("host_busy_s", ctypes.c_double)]
+                ("budget_bytes", ctypes.c_longlong), ("wall_s", ctypes.c_double), ("host_busy_s", ctypes.c_double),
+                ("max_yield_s", ctypes.c_double), ("max_iter_s", ctypes.c_double), ("yields_over_1ms", ctypes.c_int)]
 
 
 def load(build_if_missing: bool = False):

@@ -347,7 +347,8 @@ constexpr int kTileSlots = (31 * kRun + 31) / 32;
 __device__ __forceinline__ float byte_of(unsigned v, int e) { return (float)((v >> (8 * e)) & 0xffu); }
 
 // Row-like window of line `ln`, positions ws .. ws+len-1 all inside [0, N):
-// float samples in 16-byte vectors, 8-bit samples in 16-byte vectors of 16.
+// float samples in 16-byte vectors, 16-bit samples in vectors of 8, 8-bit samples in
+// vectors of 16.
 __device__ __forceinline__ bool load_window_row_vec(float *buf, const Lines &v, int ln, int N, int ws, int len,
                                                     int lane)
 {
@@ -400,6 +401,35 @@ __device__ __forceinline__ bool load_window_row_vec(float *buf, const Lines &v, 
                     const int q = 16 * k + e - off;
                     if (q >= 0 && q < len)
                         buf[pad_index(q)] = byte_of(w4[e >> 2], e & 3);
+                }
+            }
+        }
+        return true;
+    }
+    if (v.dtype == DT_F16) {
+        const __half *row = static_cast<const __half *>(v.ptr) + ln * (int)v.line_step;
+        const int a = ws & ~7, off = ws - a, nv = (off + len + 7) >> 3;
+        if (a < 0 || a + 8 * nv > N || (reinterpret_cast<uintptr_t>(row + a) & 15) != 0)
+            return false;
+        const uint4 *src = reinterpret_cast<const uint4 *>(row + a);
+        constexpr int J = (kWindowSlots * 32 + 255) / 256 + 1;
+        uint4 r[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            if (lane + 32 * j < nv)
+                r[j] = __ldg(src + lane + 32 * j);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            if (k < nv) {
+                const unsigned w4[4] = {r[j].x, r[j].y, r[j].z, r[j].w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int q = 8 * k + e - off;
+                    if (q >= 0 && q < len) {
+                        const __half2 hh = *reinterpret_cast<const __half2 *>(&w4[e >> 1]);
+                        buf[pad_index(q)] = (e & 1) ? __high2float(hh) : __low2float(hh);
+                    }
                 }
             }
         }

@@ -558,6 +558,7 @@ int snlm_server_drain(snlm_server *s)
     const auto h0 = std::chrono::steady_clock::now();
     double idle = 0.0;
     while (s->next < s->order.size() || !s->queue.empty() || !s->inflight.empty()) {
+        const auto i0 = std::chrono::steady_clock::now();
         const double now = s->clock();
         while (s->next < s->order.size() && s->reqs[s->order[s->next]].r.t_arrival <= now)
             s->queue.push_back(s->order[s->next++]);
@@ -565,14 +566,18 @@ int snlm_server_drain(snlm_server *s)
         progress |= retire(s, &err);
         if (err != SNLM_OK)
             break;
+        const auto i1 = std::chrono::steady_clock::now();
+        s->st.max_iter_s = std::max(s->st.max_iter_s, std::chrono::duration<double>(i1 - i0).count());
         if (!progress) {
             // Nothing to do until an arrival or a completion: poll again after yielding
             // the core. The loop never sleeps: a timed sleep overshot by up to ~10 ms on
             // the shared host, which over a 2000-request schedule set the p99 of the
             // lightly loaded points (17 ms at 0.2x of capacity).
-            const auto w0 = std::chrono::steady_clock::now();
             std::this_thread::yield();
-            idle += std::chrono::duration<double>(std::chrono::steady_clock::now() - w0).count();
+            const double y = std::chrono::duration<double>(std::chrono::steady_clock::now() - i1).count();
+            idle += y;
+            s->st.max_yield_s = std::max(s->st.max_yield_s, y);
+            s->st.yields_over_1ms += y > 1e-3 ? 1 : 0;
         }
     }
     if (err != SNLM_OK) {

@@ -120,6 +120,7 @@ def _footprint(r: Request) -> int:
 @dataclass
 class ServeStats:
     latencies: list = field(default_factory=list)
+    sizes: list = field(default_factory=list)      # image height of each latency
     steps: int = 0
     max_inflight: int = 0
     max_batch: int = 0
@@ -127,6 +128,7 @@ class ServeStats:
     images: int = 0
     max_used: int = 0           # peak device bytes of admitted requests
     host_s: dict = field(default_factory=lambda: {"admit": 0.0, "launch": 0.0, "retire": 0.0})
+    loop: dict = field(default_factory=dict)        # native loop: longest yield and work pass
 
     def summary(self):
         lat = np.asarray(self.latencies) * 1e3
@@ -136,7 +138,21 @@ class ServeStats:
                 "mean_ms": float(lat.mean()) if len(lat) else None, "steps": self.steps,
                 "max_batch": self.max_batch, "max_inflight_steps": self.max_inflight,
                 "peak_admitted_bytes": self.max_used,
-                "host_ms": {k: v * 1e3 for k, v in self.host_s.items()}}
+                "host_ms": {k: v * 1e3 for k, v in self.host_s.items()},
+                "by_size": self.by_size(), "loop": dict(self.loop)}
+
+    def by_size(self):
+        """Count, p50 and p99 of the latencies (ms) per image height."""
+        lat = np.asarray(self.latencies) * 1e3
+        sz = np.asarray(self.sizes)
+        out = {}
+        if len(sz) != len(lat):
+            return out
+        for v in sorted(set(self.sizes)):
+            x = lat[sz == v]
+            out[str(v)] = {"n": int(len(x)), "p50_ms": float(np.percentile(x, 50)),
+                           "p99_ms": float(np.percentile(x, 99))}
+        return out
 
 
 class Server:
@@ -265,6 +281,7 @@ class Server:
                 for (r, d_in, d_out, _, need) in e["members"]:
                     r.t_done = t_done
                     stats.latencies.append(r.latency())
+                    stats.sizes.append(r.shape[0])
                     used -= need
                 stats.images += len(e["members"])
                 if e["batch"] is not None:
@@ -301,6 +318,7 @@ def run_plain(schedule, device=None, stats: ServeStats | None = None):
         st.synchronize()
         r.t_done = time.perf_counter() - t0
         stats.latencies.append(r.latency())
+        stats.sizes.append(r.shape[0])
         stats.images += 1
     stats.wall = time.perf_counter() - t0
     return stats
@@ -337,10 +355,13 @@ class NativeServer:
             for i, r in zip(ids, schedule):
                 r.t_done, r.step = api.snlm_server_result(handle, i)
                 stats.latencies.append(r.latency())
+                stats.sizes.append(r.shape[0])
             st = api.snlm_server_get_stats(handle)
             stats.images, stats.steps, stats.max_batch = st["images"], st["launches"], st["max_batch"]
             stats.max_inflight, stats.max_used, stats.wall = st["max_inflight"], st["max_used_bytes"], st["wall_s"]
             stats.host_s = {"loop": st["host_busy_s"]}
+            stats.loop = {"max_yield_ms": st["max_yield_s"] * 1e3, "max_iter_ms": st["max_iter_s"] * 1e3,
+                          "yields_over_1ms": st["yields_over_1ms"]}
         finally:
             api.snlm_server_destroy(handle)
         return stats
