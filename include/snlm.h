@@ -288,7 +288,7 @@ int snlm_sure_combine(const float *f_rc, const float *f_cr, long long n, double 
  *  - Every call looks up the scratch area's device address in the context that is
  *    current (a host-side query, so a reset device or another context on the same
  *    device is handled). The first call in a context may load the library's device
- *    code; make that first call before capturing any stream.
+ *    code, unless snlm_preload loaded it beforehand.
  *  - All calls in the process share the scratch area. Calls whose device work can
  *    overlap in time (several streams, or several host threads without ordering)
  *    race on it and corrupt each other's results: serialise them.
@@ -467,7 +467,8 @@ typedef struct {
 typedef struct snlm_server snlm_server;
 
 /* cfg may be NULL (defaults: batched, half the free memory, 4 streams, 256 per batch,
- * 1<<20 solo pixels). SNLM_ERR_NOMEM if the slab cannot be allocated. */
+ * 1<<20 solo pixels). Loads every kernel first (snlm_preload): SNLM_ERR_CUDA if that
+ * fails. SNLM_ERR_NOMEM if the slab cannot be allocated. */
 int snlm_server_create(const snlm_server_config *cfg, snlm_server **server);
 /* Validates and queues n requests (host pointers stay owned by the caller and must
  * stay valid until the drain that serves them returns); ids[i] (may be NULL)
@@ -520,6 +521,21 @@ long long snlm_get_option(int option);
  * else SNLM_OK; the record is cleared. snlm_denoise_host checks it itself.
  */
 int snlm_device_error(void *stream);
+
+/*
+ * Loads the device code of every kernel the library launches, on the current device
+ * (no counterpart in the paper). Under lazy module loading, CUDA's default, a kernel
+ * is otherwise loaded by its first launch: inside the caller's launch sequence, where
+ * the load holds the calling thread, and measured on a GB300 it delayed the work
+ * already in flight by 5-90 ms. Call it once per context before latency-sensitive
+ * work (a serving loop, before capturing a CUDA graph, before the first
+ * snlm_denoise_noalloc of a real-time loop); snlm_server_create calls it. A kernel
+ * that is already loaded costs a lookup, so repeated calls are cheap. *n_loaded (may
+ * be NULL) receives the number of kernels loaded, SNLM_KERNEL_COUNT when all were.
+ * Returns SNLM_OK, or SNLM_ERR_CUDA if some kernel could not be loaded.
+ */
+#define SNLM_KERNEL_COUNT 198
+int snlm_preload(int *n_loaded);
 
 #ifdef __cplusplus
 }

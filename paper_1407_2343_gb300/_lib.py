@@ -79,6 +79,8 @@ def load(build_if_missing: bool = False):
         lib.snlm_status_str.restype = ctypes.c_char_p
         lib.snlm_version.argtypes = []
         lib.snlm_version.restype = ci
+        lib.snlm_preload.argtypes = [ctypes.POINTER(ci)]
+        lib.snlm_preload.restype = ci
         lib.snlm_default_h.argtypes = [cf, ci, ci, cf]
         lib.snlm_default_h.restype = cf
         lib.snlm_workspace_bytes.argtypes = [ci, ci, ci]
@@ -174,5 +176,5 @@ EXPORTED = [
     "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
     "snlm_set_option", "snlm_get_option", "snlm_device_error", "snlm_server_create", "snlm_server_submit",
     "snlm_server_drain", "snlm_server_result", "snlm_server_get_stats", "snlm_server_clock", "snlm_server_destroy",
-    "snlm_probe_peaks", "snlm_sure_band", "snlm_sure_theta", "snlm_sure_combine",
+    "snlm_probe_peaks", "snlm_sure_band", "snlm_sure_theta", "snlm_sure_combine", "snlm_preload",
 ]

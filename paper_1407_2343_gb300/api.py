@@ -74,6 +74,17 @@ def snlm_version() -> int:
     return int(_lib.load().snlm_version())
 
 
+KERNEL_COUNT = 198   # SNLM_KERNEL_COUNT of include/snlm.h
+
+
+def snlm_preload() -> int:
+    """Load every kernel of the library on the current device (see include/snlm.h);
+    returns how many were loaded."""
+    n = ctypes.c_int(0)
+    _check(_lib.load().snlm_preload(ctypes.byref(n)), "snlm_preload")
+    return int(n.value)
+
+
 def snlm_default_h(sigma: float, K: int, profile="box", beta: float = 0.0) -> float:
     return float(_lib.load().snlm_default_h(float(sigma), int(K), _profile(profile), float(beta or 0.0)))
 

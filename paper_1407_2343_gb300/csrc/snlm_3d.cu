@@ -55,6 +55,13 @@ int grid_for(long long items, int per_block)
 
 }  // namespace
 
+int preload_3d()
+{
+    return preload_kernel((const void *)swap_outer_kernel<unsigned char>) +
+           preload_kernel((const void *)swap_outer_kernel<__half>) +
+           preload_kernel((const void *)swap_outer_kernel<float>) + preload_kernel((const void *)axpby_kernel);
+}
+
 cudaError_t launch_swap_outer(const void *in, int dtype, float *out, int A, int B, int W, cudaStream_t st)
 {
     const int grid = grid_for((long long)A * B, 1);

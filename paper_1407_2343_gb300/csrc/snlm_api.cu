@@ -359,6 +359,19 @@ const char *snlm_status_str(int status)
 
 int snlm_version(void) { return 100; }
 
+int snlm_preload(int *n_loaded)
+{
+    const int n = preload_pass<0>() + preload_pass<1>() + preload_pass<2>() + preload_pass<3>() +
+                  preload_pass<4>() + preload_pass<5>() + preload_pass<6>() + preload_pass<7>() +
+                  preload_pass_tma<0>() + preload_pass_tma<1>() + preload_pass_tma<2>() + preload_pass_tma<3>() +
+                  preload_pass_tma<4>() + preload_pass_tma<5>() + preload_pass_tma<6>() + preload_pass_tma<7>() +
+                  preload_batch() + preload_iir() + preload_sure() + preload_bilateral() + preload_nlm2d() +
+                  preload_3d();
+    if (n_loaded)
+        *n_loaded = n;
+    return n == SNLM_KERNEL_COUNT ? SNLM_OK : SNLM_ERR_CUDA;
+}
+
 float snlm_default_h(float sigma, int K, int profile, float beta)
 {
     if (!(sigma >= 0.f) || K < 0 || K > 64)

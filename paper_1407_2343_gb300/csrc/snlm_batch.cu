@@ -73,6 +73,15 @@ struct ClassInfo {
 };
 
 }  // namespace
+
+int preload_batch()
+{
+    int n = 0;
+    for (int K = 1; K <= 7; ++K)
+        n += preload_kernel((const void *)batch_fn(K));
+    return n;
+}
+
 }  // namespace snlm
 
 using namespace snlm;

@@ -19,6 +19,8 @@
 #include "snlm_host.h"
 #include "snlm_internal.h"
 
+#include <utility>
+
 namespace snlm {
 
 namespace {
@@ -207,6 +209,12 @@ cudaError_t launch_bf(const BfArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int... R>
+int preload_bf(std::integer_sequence<int, R...>)
+{
+    return (preload_kernel((const void *)bilateral_kernel<R>) + ...);
+}
+
 bool overlaps(const float *a, long long na, const float *b, long long nb)
 {
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
@@ -272,6 +280,11 @@ int check_bilateral(const float *in, int H, int W, long long in_pitch, float sig
     if (overlaps(in, (long long)(H - 1) * in_pitch + W, out, (long long)(H - 1) * out_pitch + W))
         return SNLM_ERR_ARG;
     return SNLM_OK;
+}
+
+int preload_bilateral()
+{
+    return preload_bf(std::make_integer_sequence<int, 8>{});
 }
 
 }  // namespace snlm

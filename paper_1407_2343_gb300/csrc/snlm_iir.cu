@@ -506,6 +506,13 @@ void iir_lag_weights(double beta, int S, float *geff)
 
 }  // namespace
 
+int preload_iir()
+{
+    return preload_kernel((const void *)iir_pass_kernel<kIirPass>) +
+           preload_kernel((const void *)iir_pass_kernel<kIirDist>) +
+           preload_kernel((const void *)iir_pass_kernel<kIirSure>);
+}
+
 int iir_check_beta(double beta)
 {
     IirArgs a;

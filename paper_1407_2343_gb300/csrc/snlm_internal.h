@@ -203,4 +203,27 @@ cudaError_t launch_image_sums(const float *frc, const float *fcr, const Lines &f
 cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out, long long n, double theta1,
                                  double theta2, cudaStream_t st);
 
+// ---- Loading the device code up front (snlm_preload). Under lazy module loading,
+// CUDA's default, a kernel is loaded by its first launch, inside the caller's launch
+// sequence, where the load can hold the calling thread and the work in flight for
+// milliseconds. Each preload_* loads every kernel its file launches on the current
+// device and returns how many it loaded; a kernel that is already loaded costs a
+// lookup.
+inline int preload_kernel(const void *f)
+{
+    cudaFuncAttributes attr;
+    if (cudaFuncGetAttributes(&attr, f) == cudaSuccess)
+        return 1;
+    cudaGetLastError();
+    return 0;
+}
+template <int K> int preload_pass();       // snlm_pass_k<K>.cu: pass and distance kernels
+template <int K> int preload_pass_tma();   // snlm_pass_k<K>.cu: TMA pass kernels
+int preload_batch();                       // snlm_batch.cu
+int preload_iir();                         // snlm_iir.cu
+int preload_sure();                        // snlm_sure.cu
+int preload_bilateral();                   // snlm_bilateral.cu
+int preload_nlm2d();                       // snlm_nlm2d.cu
+int preload_3d();                          // snlm_3d.cu
+
 }  // namespace snlm

@@ -19,6 +19,8 @@
 #include "snlm_host.h"
 #include "snlm_internal.h"
 
+#include <utility>
+
 #include <cuda_fp16.h>
 
 namespace snlm {
@@ -188,7 +190,18 @@ cudaError_t launch_n2(const Nlm2dArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int... K>
+int preload_n2(std::integer_sequence<int, K...>)
+{
+    return (preload_kernel((const void *)nlm2d_kernel<K>) + ...);
+}
+
 }  // namespace
+
+int preload_nlm2d()
+{
+    return preload_n2(std::make_integer_sequence<int, 8>{});
+}
 
 }  // namespace snlm
 

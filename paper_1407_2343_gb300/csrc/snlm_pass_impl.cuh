@@ -1531,8 +1531,35 @@ cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st)
     }
 }
 
+// The kernels launch_pass and launch_dist dispatch to, and no others.
+template <int K>
+int preload_pass()
+{
+    const void *f[] = {
+        (const void *)nlm_pass_kernel<K, DIST_SLIDE, false, LOAD_GATHER>,
+        (const void *)nlm_pass_kernel<K, DIST_SLIDE, true, LOAD_ASYNC_STAGED>,
+        (const void *)nlm_pass_kernel<K, DIST_SLIDE, true, LOAD_GATHER>,
+        (const void *)nlm_pass_kernel<K, DIST_BLOCK, false, LOAD_GATHER>,
+        (const void *)nlm_pass_kernel<K, DIST_BLOCK, true, LOAD_ASYNC_F32>,
+        (const void *)nlm_pass_kernel<K, DIST_BLOCK, true, LOAD_ASYNC_STAGED>,
+        (const void *)nlm_pass_kernel<K, DIST_BLOCK, true, LOAD_GATHER>,
+        (const void *)nlm_pass_kernel<K, DIST_FIR, false, LOAD_GATHER>,
+        (const void *)nlm_pass_kernel<K, DIST_FIR, true, LOAD_ASYNC_F32>,
+        (const void *)nlm_pass_kernel<K, DIST_FIR, true, LOAD_ASYNC_STAGED>,
+        (const void *)nlm_pass_kernel<K, DIST_FIR, true, LOAD_GATHER>,
+        (const void *)patch_dist_kernel<K, DIST_SLIDE>,
+        (const void *)patch_dist_kernel<K, DIST_BLOCK>,
+        (const void *)patch_dist_kernel<K, DIST_FIR>,
+    };
+    int n = 0;
+    for (const void *k : f)
+        n += preload_kernel(k);
+    return n;
+}
+
 }  // namespace snlm
 
 #define SNLM_INSTANTIATE_K(KK)                                                                       \
     template cudaError_t snlm::launch_pass<KK>(const snlm::PassArgs &, int, bool, cudaStream_t);     \
-    template cudaError_t snlm::launch_dist<KK>(const snlm::DistArgs &, int, cudaStream_t);
+    template cudaError_t snlm::launch_dist<KK>(const snlm::DistArgs &, int, cudaStream_t);           \
+    template int snlm::preload_pass<KK>();

@@ -397,9 +397,25 @@ cudaError_t pass_tma_occupancy(int dist_mode, bool sure, int smem, int *n)
     }
 }
 
+// The kernels launch_pass_tma dispatches to.
+template <int K>
+int preload_pass_tma()
+{
+    const void *f[] = {
+        (const void *)nlm_pass_tma_kernel<K, DIST_SLIDE, false>, (const void *)nlm_pass_tma_kernel<K, DIST_SLIDE, true>,
+        (const void *)nlm_pass_tma_kernel<K, DIST_BLOCK, false>, (const void *)nlm_pass_tma_kernel<K, DIST_BLOCK, true>,
+        (const void *)nlm_pass_tma_kernel<K, DIST_FIR, false>,   (const void *)nlm_pass_tma_kernel<K, DIST_FIR, true>,
+    };
+    int n = 0;
+    for (const void *k : f)
+        n += preload_kernel(k);
+    return n;
+}
+
 }  // namespace snlm
 
 #define SNLM_INSTANTIATE_TMA_K(KK)                                                                             \
     template cudaError_t snlm::launch_pass_tma<KK>(const snlm::PassArgs &, const snlm::TmaPass &, int, bool, int, \
                                                    cudaStream_t);                                              \
-    template cudaError_t snlm::pass_tma_occupancy<KK>(int, bool, int, int *);
+    template cudaError_t snlm::pass_tma_occupancy<KK>(int, bool, int, int *);                               \
+    template int snlm::preload_pass_tma<KK>();

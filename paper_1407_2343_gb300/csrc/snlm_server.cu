@@ -473,6 +473,10 @@ int snlm_server_create(const snlm_server_config *cfg, snlm_server **out)
         return SNLM_ERR_ARG;
     if (c.mode == SNLM_SERVE_PLAIN)
         c.streams = 1;
+    // every kernel a request can reach is loaded now, not by its first launch in the
+    // loop (a lazy load there held the loop and the work in flight for 5-90 ms)
+    if (snlm_preload(nullptr) != SNLM_OK)
+        return SNLM_ERR_CUDA;
     snlm_server *s = new snlm_server();
     s->cfg = c;
     memset(&s->st, 0, sizeof(s->st));

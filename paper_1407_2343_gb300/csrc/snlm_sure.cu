@@ -157,6 +157,18 @@ __global__ void set_theta_kernel(double *info, double t0, double t1)
 
 }  // namespace
 
+int preload_sure()
+{
+    const void *f[] = {(const void *)sure_partial_kernel, (const void *)sure_solve_kernel,
+                       (const void *)combine_kernel,      (const void *)combine_scalar_kernel,
+                       (const void *)sure_sums_kernel,    (const void *)combine_theta_kernel,
+                       (const void *)image_sums_kernel,   (const void *)set_theta_kernel};
+    int n = 0;
+    for (const void *k : f)
+        n += preload_kernel(k);
+    return n;
+}
+
 cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
                               double sigma2, double *info, double *scratch, cudaStream_t st)
 {

@@ -341,3 +341,12 @@ def test_full_size_whole_image_parity(dev, api, orc):
     # patch distances of the first rows, bit exact
     d = np_of(api.snlm_patch_dist_1d(t[:4], S, K, "box"))
     np.testing.assert_array_equal(d, orc.patch_dist_1d(img[:4].astype(np.float64), S, K, "box").astype(np.int64))
+
+
+def test_preload_loads_every_kernel(dev, api):
+    import time
+
+    assert api.snlm_preload() == api.KERNEL_COUNT
+    t0 = time.perf_counter()
+    assert api.snlm_preload() == api.KERNEL_COUNT      # already loaded: lookups only
+    assert time.perf_counter() - t0 < 0.5
