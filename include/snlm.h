@@ -525,11 +525,10 @@ int snlm_device_error(void *stream);
 /*
  * Loads the device code of every kernel the library launches, on the current device
  * (no counterpart in the paper). Under lazy module loading, CUDA's default, a kernel
- * is otherwise loaded by its first launch: inside the caller's launch sequence, where
- * the load holds the calling thread, and measured on a GB300 it delayed the work
- * already in flight by 5-90 ms. Call it once per context before latency-sensitive
- * work (a serving loop, before capturing a CUDA graph, before the first
- * snlm_denoise_noalloc of a real-time loop); snlm_server_create calls it. A kernel
+ * is otherwise loaded by its first launch, inside the caller's launch sequence, which
+ * then holds the calling thread for the load. Call it once per context before
+ * latency-sensitive work (a serving loop, the first snlm_denoise_noalloc of a
+ * real-time loop); snlm_server_create calls it. A kernel
  * that is already loaded costs a lookup, so repeated calls are cheap. *n_loaded (may
  * be NULL) receives the number of kernels loaded, SNLM_KERNEL_COUNT when all were.
  * Returns SNLM_OK, or SNLM_ERR_CUDA if some kernel could not be loaded.

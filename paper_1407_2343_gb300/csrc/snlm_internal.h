@@ -205,8 +205,8 @@ cudaError_t launch_combine_theta(const float *frc, const float *fcr, float *out,
 
 // ---- Loading the device code up front (snlm_preload). Under lazy module loading,
 // CUDA's default, a kernel is loaded by its first launch, inside the caller's launch
-// sequence, where the load can hold the calling thread and the work in flight for
-// milliseconds. Each preload_* loads every kernel its file launches on the current
+// sequence, where the load holds the calling thread. Each preload_* loads every
+// kernel its file launches on the current
 // device and returns how many it loaded; a kernel that is already loaded costs a
 // lookup.
 inline int preload_kernel(const void *f)

@@ -178,8 +178,13 @@ bool stage_request(snlm_server *s, Launch &L, const snlm_serve_request &r, cudaS
     L.mem.push_back({a, in_bytes(r)});
     L.mem.push_back({b, out_bytes(r)});
     const size_t es = snlm::dtype_size(r.dtype);
-    cudaMemcpy2DAsync(a, (size_t)r.W * es, r.img, (size_t)r.pitch * es, (size_t)r.W * es, (size_t)r.H,
-                      cudaMemcpyHostToDevice, st);
+    // a dense image goes as one linear copy; only a pitched one needs the 2-D form
+    // (one row per copy-engine line)
+    if (r.pitch == r.W)
+        cudaMemcpyAsync(a, r.img, in_bytes(r), cudaMemcpyHostToDevice, st);
+    else
+        cudaMemcpy2DAsync(a, (size_t)r.W * es, r.img, (size_t)r.pitch * es, (size_t)r.W * es, (size_t)r.H,
+                          cudaMemcpyHostToDevice, st);
     *d_in = a;
     *d_out = static_cast<float *>(b);
     return true;
@@ -473,8 +478,8 @@ int snlm_server_create(const snlm_server_config *cfg, snlm_server **out)
         return SNLM_ERR_ARG;
     if (c.mode == SNLM_SERVE_PLAIN)
         c.streams = 1;
-    // every kernel a request can reach is loaded now, not by its first launch in the
-    // loop (a lazy load there held the loop and the work in flight for 5-90 ms)
+    // every kernel a request can reach is loaded now, not by its first launch inside
+    // the loop
     if (snlm_preload(nullptr) != SNLM_OK)
         return SNLM_ERR_CUDA;
     snlm_server *s = new snlm_server();
