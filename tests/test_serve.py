@@ -29,6 +29,17 @@ def test_schedule_statistics():
             assert r.h == pytest.approx(r.sigma * math.sqrt(2 * r.K + 1), rel=1e-6)
 
 
+def test_stats_split_latencies_by_image_size():
+    st = serve.ServeStats(latencies=[0.001, 0.003, 0.002, 0.010, 0.030], sizes=[128, 128, 128, 4096, 4096],
+                          wall=1.0, images=5)
+    by = st.summary()["by_size"]
+    assert set(by) == {"128", "4096"}
+    assert by["128"]["n"] == 3 and by["128"]["p50_ms"] == pytest.approx(2.0)
+    assert by["4096"]["n"] == 2 and by["4096"]["p99_ms"] == pytest.approx(29.8)
+    # a run that recorded no sizes reports none
+    assert serve.ServeStats(latencies=[0.001], wall=1.0, images=1).summary()["by_size"] == {}
+
+
 @pytest.fixture(scope="module")
 def dev():
     import torch
