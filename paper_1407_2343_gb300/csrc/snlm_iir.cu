@@ -49,7 +49,7 @@ namespace {
 
 constexpr int kIirRun = 16;                      // positions per lane
 constexpr int kIirSpan = 32 * kIirRun;           // positions per warp window
-constexpr int kIirWarps = 8;                     // lines per CTA
+constexpr int kIirWarps = 4;                     // lines per CTA
 constexpr int kIirMaxWarm = 64;                  // history a position may need (58 at beta = 3.5)
 constexpr int kIirMaxRounds = 2;                 // scan rounds (16 * 2^rounds >= warm)
 
@@ -251,9 +251,13 @@ __device__ __forceinline__ void iir_filter_run(const float (&dl)[kIirRun], float
 // each lag (reading R17): per pixel x and offset s the patch term takes
 // w(x, s) g(s) (a_s - mu) a_-s + w(x-s, s) g(s) (a_-s - mu) a_s, a_s = f(x+s) - f(x),
 // kept as TA - mu TB; the owner of x reads f(x-s) from the window row and w(x-s, s)
-// from the pushed weights. Three more accumulators per position: one CTA per SM.
+// from the pushed weights. Occupancy: CTAs of 4 warps (warps work independently,
+// so small CTAs fill the SMs evenly); 4 per SM for the plain passes (128 registers),
+// 3 for SURE (168 registers: its three more accumulators per position spill a few
+// words there, and 16 warps at 128 registers spill ~0.5 KB; 12 warps measured 13 %
+// faster than 8 at 255 registers).
 template <int MODE>
-__global__ void __launch_bounds__(kIirWarps * 32, MODE == kIirSure ? 1 : 2) iir_pass_kernel(const IirArgs a)
+__global__ void __launch_bounds__(kIirWarps * 32, MODE == kIirSure ? 3 : 4) iir_pass_kernel(const IirArgs a)
 {
     constexpr bool DIST = MODE == kIirDist;
     constexpr bool SURE = MODE == kIirSure;
@@ -475,7 +479,7 @@ cudaError_t launch_iir(const IirArgs &a, int mode, cudaStream_t st)
     const int groups = div_up(a.n_lines, kIirWarps);
     const dim3 grid((unsigned)tiles, (unsigned)(groups < 65535 ? groups : 65535));
     const bool dist = mode == kIirDist;
-    const int smem = kIirWarps * (dist ? 1 : 3) * kIirRow * (int)sizeof(float);   // 66 KB (pass), 22 KB
+    const int smem = kIirWarps * (dist ? 1 : 3) * kIirRow * (int)sizeof(float);   // 33 KB (pass), 11 KB
     if (mode == kIirDist)
         return launch_iir_t<kIirDist>(a, grid, smem, st);
     if (mode == kIirSure)
