@@ -47,15 +47,15 @@ OPS_PER_PAIR = {"plain": 9, "sure": 11}
 OPS_PER_PAIR_IIR = 15
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# pass kernels of the 4096^2 u8 SURE step, from one ncu --set full capture of
-# `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
+# pass kernels of the 4096^2 u8 SURE step, from one ncu capture of those two
+# metrics (`-k regex:nlm_pass_kernel -s 12 -c 4`: the first timed step's four
+# passes) of `python bench.py --steps 2 --warmup 3 --no-batch --no-serve --no-e2e
 # --no-cpu-baseline --no-rc --no-bf --no-nlm2d --no-3d --no-iir --no-fp16
-# --no-precision` (the first timed step's four passes); valid only while the
-# pass kernels' sources (PASS_KERNEL_SOURCES) hash to `sources_sha` (profiles/ has
-# the capture's summary).
-TRAFFIC = {"sources_sha": "f6ed7b21fb79dc29",
-           "bytes_per_launch": {"row_pass_sure/slide": 90699776, "col_pass_sure/block": 179043840,
-                                "col_pass_sure/slide": 96404480, "row_pass_sure/block": 268333056}}
+# --no-precision`; valid only while the pass kernels' sources (PASS_KERNEL_SOURCES)
+# hash to `sources_sha` (profiles/ has the capture's summary).
+TRAFFIC = {"sources_sha": "11ccc9ab695ad27c",
+           "bytes_per_launch": {"row_pass_sure/slide": 89504768, "col_pass_sure/block": 175620608,
+                                "col_pass_sure/slide": 92700416, "row_pass_sure/block": 264653056}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:

@@ -1314,16 +1314,23 @@ __device__ __forceinline__ void process_tile(const PassArgs &p, int bid, float *
 }
 
 // CTAs per SM the compiler is held to (registers per thread = 65536 / (128 x this)),
-// chosen per variant by measurement on GB300: the plain running-sum pass is fastest
-// at 5 (96 registers) up to K = 5 and at 4 beyond (96 registers spill there); the
-// float and SURE passes at 4 (128 registers), the SURE passes at 3 (168 registers)
-// from K = 7, where 128 registers spill (21 % faster at 4096^2, S = 20).
+// chosen per variant by measuring 4096^2 passes at S = 10 and 20 on GB300. Plain
+// passes: 5 (96 registers) while the variant fits them with few or no spills, else 4
+// (128 registers): the running-sum pass up to K = 4 (2-9 % faster than at 4; at K = 5
+// 4 is 4 % faster), the float block-sum pass up to K = 3 (up to 8 % faster; 4-36 %
+// slower beyond), the Gaussian pass up to K = 5 (1-7 % faster; 3-11 % slower
+// beyond). SURE passes: 4 (128 registers; 18 % slower at 3), and 3 (168 registers)
+// from K = 7, where 128 registers spill (21 % faster at S = 20).
 template <int K, int DM, bool SURE>
 constexpr int pass_min_ctas()
 {
     if (SURE)
         return K >= 7 ? 3 : 4;
-    return (DM != DIST_SLIDE || K >= 6) ? 4 : 5;
+    if (DM == DIST_SLIDE)
+        return K <= 4 ? 5 : 4;
+    if (DM == DIST_BLOCK)
+        return K <= 3 ? 5 : 4;
+    return K <= 5 ? 5 : 4;
 }
 
 template <int K, int DM, bool SURE, int LOADER>
