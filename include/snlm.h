@@ -351,6 +351,14 @@ int snlm_batch_plan_capture(snlm_batch_plan *plan, void *stream);
 /* Waits for `stream`, then reports whether a bounded wait gave up in the last run
  * (SNLM_ERR_TIMEOUT) and clears the flag. */
 int snlm_batch_plan_status(snlm_batch_plan *plan, void *stream);
+/* The same report without waiting: enqueues on `stream` a copy of the plan's
+ * failure word into *host_word and returns. Once the stream has passed that point
+ * (an event recorded after this call has completed), *host_word != 0 means a
+ * bounded wait of the runs enqueued before it gave up. host_word should be pinned
+ * host memory (cudaHostAlloc); with pageable memory CUDA performs the copy
+ * synchronously. SNLM_ERR_ARG for a NULL plan, a plan without workspace or a NULL
+ * host_word. */
+int snlm_batch_plan_status_async(snlm_batch_plan *plan, int *host_word, void *stream);
 /* Number of jobs, units and K classes of the plan (any pointer may be NULL). */
 int snlm_batch_plan_info(const snlm_batch_plan *plan, int *jobs, int *units, int *classes);
 void snlm_batch_plan_destroy(snlm_batch_plan *plan);

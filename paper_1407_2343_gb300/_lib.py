@@ -128,6 +128,8 @@ def load(build_if_missing: bool = False):
         lib.snlm_batch_plan_capture.argtypes = [vp, vp]
         lib.snlm_batch_plan_capture.restype = ci
         lib.snlm_batch_plan_status.argtypes = [vp, vp]
+        lib.snlm_batch_plan_status_async.argtypes = [vp, vp, vp]
+        lib.snlm_batch_plan_status_async.restype = ci
         lib.snlm_batch_plan_status.restype = ci
         lib.snlm_batch_plan_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
         lib.snlm_batch_plan_info.restype = ci
@@ -173,7 +175,8 @@ EXPORTED = [
     "snlm_denoise_bf", "snlm_nlm_2d", "snlm_denoise_3d", "snlm_nlm_1d", "snlm_patch_dist_1d", "snlm_trace_enable",
     "snlm_trace_read", "snlm_kernel_name", "snlm_denoise_noalloc", "snlm_batch_plan_create",
     "snlm_batch_plan_workspace_bytes", "snlm_batch_plan_upload", "snlm_batch_plan_launch",
-    "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_info", "snlm_batch_plan_destroy",
+    "snlm_batch_plan_capture", "snlm_batch_plan_status", "snlm_batch_plan_status_async", "snlm_batch_plan_info",
+    "snlm_batch_plan_destroy",
     "snlm_set_option", "snlm_get_option", "snlm_device_error", "snlm_server_create", "snlm_server_submit",
     "snlm_server_drain", "snlm_server_result", "snlm_server_get_stats", "snlm_server_clock", "snlm_server_destroy",
     "snlm_probe_peaks", "snlm_sure_band", "snlm_sure_theta", "snlm_sure_combine", "snlm_preload",

@@ -503,6 +503,16 @@ def snlm_batch_plan_status(plan, stream=None) -> int:
     return int(_lib.load().snlm_batch_plan_status(ctypes.c_void_p(plan), _stream_ptr(stream)))
 
 
+def snlm_batch_plan_status_async(plan, host_word, stream=None):
+    """Enqueue a copy of the plan's failure word into `host_word` (a pinned int32
+    host tensor of at least one element) on the stream, without waiting; nonzero
+    there, once the stream has passed this point, means a bounded wait gave up."""
+    if host_word.dtype != _torch().int32 or host_word.device.type != "cpu" or host_word.numel() < 1:
+        raise ValueError("host_word must be an int32 host tensor with at least one element")
+    _check(_lib.load().snlm_batch_plan_status_async(ctypes.c_void_p(plan), ctypes.c_void_p(host_word.data_ptr()),
+                                                    _stream_ptr(stream)), "snlm_batch_plan_status_async")
+
+
 def snlm_batch_plan_info(plan):
     j, u, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_lib.load().snlm_batch_plan_info(ctypes.c_void_p(plan), ctypes.byref(j), ctypes.byref(u),

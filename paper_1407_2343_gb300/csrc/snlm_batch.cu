@@ -11,6 +11,7 @@
 // They are bounded anyway (a time limit read from %globaltimer); a CTA that gives
 // up records it in the control block and stops taking work.
 #include <algorithm>
+#include <cstddef>
 #include <memory>
 #include <numeric>
 
@@ -547,6 +548,15 @@ int snlm_batch_plan_status(snlm_batch_plan *P, void *stream)
     if (e != cudaSuccess)
         return status_of(e);
     return ctl.err ? SNLM_ERR_TIMEOUT : SNLM_OK;
+}
+
+int snlm_batch_plan_status_async(snlm_batch_plan *P, int *host_word, void *stream)
+{
+    if (!P || !P->ws || !host_word)
+        return SNLM_ERR_ARG;
+    const size_t off = P->ctl_off + offsetof(BatchCtl, err);
+    return status_of(cudaMemcpyAsync(host_word, static_cast<char *>(P->ws) + off, sizeof(int),
+                                     cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)));
 }
 
 void snlm_batch_plan_destroy(snlm_batch_plan *P)

@@ -131,6 +131,7 @@ struct snlm_server {
     std::vector<cudaStream_t> streams;
     std::vector<char> busy;
     std::vector<char> high;       // stream created with the device's highest priority
+    int *status = nullptr;        // pinned: the failure word of each stream's batch launch
     std::vector<Req> reqs;
     std::vector<int> order;       // submitted ids by arrival time
     size_t next = 0;              // next entry of `order` not yet arrived
@@ -324,6 +325,10 @@ int launch_batch(snlm_server *s, const std::vector<int> &ids, int si, Launch &L,
     }
     if (rc == SNLM_OK)
         rc = snlm_batch_plan_launch(plan, st);
+    // the run's failure word lands in pinned memory behind it on the stream: read once
+    // the launch's event has completed, without a blocking readback in the loop
+    if (rc == SNLM_OK)
+        rc = snlm_batch_plan_status_async(plan, &s->status[si], st);
     if (rc != SNLM_OK) {
         cudaStreamSynchronize(st);
         release_launch(s, L);
@@ -438,10 +443,8 @@ bool retire(snlm_server *s, int *err)
         if (q != cudaSuccess) {
             cudaGetLastError();
             *err = SNLM_ERR_CUDA;
-        } else if (L.plan) {
-            const int rc = snlm_batch_plan_status(L.plan, s->streams[L.stream]);
-            if (rc != SNLM_OK)
-                *err = rc;
+        } else if (L.plan && *static_cast<volatile int *>(&s->status[L.stream]) != 0) {
+            *err = SNLM_ERR_TIMEOUT;
         }
         for (int id : L.members) {
             s->reqs[id].t_done = t;
@@ -501,6 +504,14 @@ int snlm_server_create(const snlm_server_config *cfg, snlm_server **out)
         return SNLM_ERR_NOMEM;
     }
     s->st.budget_bytes = (long long)s->slab.size;
+    void *words = nullptr;
+    if (cudaHostAlloc(&words, (size_t)c.streams * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return SNLM_ERR_NOMEM;
+    }
+    s->status = static_cast<int *>(words);
+    memset(s->status, 0, (size_t)c.streams * sizeof(int));
     s->streams.resize((size_t)c.streams);
     s->busy.assign((size_t)c.streams, 0);
     s->high.assign((size_t)c.streams, 0);
@@ -636,6 +647,8 @@ void snlm_server_destroy(snlm_server *s)
     for (auto st : s->streams)
         if (st)
             cudaStreamDestroy(st);
+    if (s->status)
+        cudaFreeHost(s->status);
     delete s;
 }
 

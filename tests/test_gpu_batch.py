@@ -170,15 +170,21 @@ def test_batch_bounded_wait_reports_timeout(dev):
 
     reqs = make_requests(dev, MIXED[:3])
     b = Batch(reqs, spin_limit_us=20000, fail_job=3)
-    b.run()
+    word = torch.full((1,), -7, dtype=torch.int32).pin_memory()
+    st = torch.cuda.current_stream()
+    b.run(st)
+    api.snlm_batch_plan_status_async(b.plan, word, st)    # the same report without waiting
     torch.cuda.synchronize()
+    assert int(word[0]) != 0
     assert b.status() == api.ERR_TIMEOUT
     b.close()
     # the context still works
     reqs2 = make_requests(dev, MIXED[:2])
     b2 = Batch(reqs2)
-    b2.run()
+    b2.run(st)
+    api.snlm_batch_plan_status_async(b2.plan, word, st)
     torch.cuda.synchronize()
+    assert int(word[0]) == 0
     assert b2.status() == api.OK
     check(reqs2)
     b2.close()
