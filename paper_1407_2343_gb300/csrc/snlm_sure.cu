@@ -105,11 +105,15 @@ __global__ void combine_theta_kernel(const float *__restrict__ frc, const float 
 }
 
 // Partial records of the SURE sums over whole images, for the passes that form no
-// records of their own (the recursive profile's): block b takes the pixels of rows
-// [r0, r1) at flat indices b*256 + t, + gridDim.x*256, ..., forms in float32
+// records of their own (the recursive profile's): block b takes rows r0 + b,
+// r0 + b + gridDim.x, ... of [r0, r1), thread t the columns t, t + 256, ... of each,
+// and forms in float32
 //   m = (frc + fcr)/2, d = (frc - fcr)/2:  m^2, m d, d^2, f m, f d, delta
-// (frc == NULL: delta only), accumulates them per thread in FP64 and reduces the
-// block in a fixed tree into record b (kPartials doubles, the unused ones zero).
+// (frc == NULL: delta only). A thread sums its at most ceil(W/256) terms of a row in
+// float32 (as the pass kernels sum a lane's run) and adds the row's partial in FP64
+// (FP64 arithmetic is slow on this GPU, so it is kept to one add per row and sum);
+// the block is reduced in a fixed tree into record b (kPartials doubles, the unused
+// ones zero).
 __global__ void __launch_bounds__(kSolveThreads) image_sums_kernel(const float *__restrict__ frc,
                                                                    const float *__restrict__ fcr, Lines f, int W,
                                                                    int r0, int r1, const float *__restrict__ delta,
@@ -117,24 +121,27 @@ __global__ void __launch_bounds__(kSolveThreads) image_sums_kernel(const float *
 {
     __shared__ double sh[kPartials * kSolveThreads];
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const long long lo = (long long)r0 * W, hi = (long long)r1 * W;
-    for (long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
-         i += (long long)gridDim.x * blockDim.x) {
-        acc[5] += (double)delta[i];
-        if (frc) {
-            const int r = (int)(i / W), c = (int)(i - (long long)r * W);
-            const float a = frc[i], b = fcr[i];
-            const float m = 0.5f * (a + b), d = 0.5f * (a - b);
-            const long long fo = (long long)r * f.line_step + c;
-            const float fv = f.dtype == DT_U8 ? (float)static_cast<const unsigned char *>(f.ptr)[fo]
-                             : f.dtype == DT_F16 ? __half2float(static_cast<const __half *>(f.ptr)[fo])
-                                                 : static_cast<const float *>(f.ptr)[fo];
-            acc[0] += (double)(m * m);
-            acc[1] += (double)(m * d);
-            acc[2] += (double)(d * d);
-            acc[3] += (double)(fv * m);
-            acc[4] += (double)(fv * d);
+    for (int r = r0 + (int)blockIdx.x; r < r1; r += (int)gridDim.x) {
+        const long long row = (long long)r * W, fo = (long long)r * f.line_step;
+        float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = (int)threadIdx.x; c < W; c += (int)blockDim.x) {
+            s[5] += delta[row + c];
+            if (frc) {
+                const float a = frc[row + c], b = fcr[row + c];
+                const float m = 0.5f * (a + b), d = 0.5f * (a - b);
+                const float fv = f.dtype == DT_U8 ? (float)static_cast<const unsigned char *>(f.ptr)[fo + c]
+                                 : f.dtype == DT_F16 ? __half2float(static_cast<const __half *>(f.ptr)[fo + c])
+                                                     : static_cast<const float *>(f.ptr)[fo + c];
+                s[0] = fmaf(m, m, s[0]);
+                s[1] = fmaf(m, d, s[1]);
+                s[2] = fmaf(d, d, s[2]);
+                s[3] = fmaf(fv, m, s[3]);
+                s[4] = fmaf(fv, d, s[4]);
+            }
         }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            acc[k] += (double)s[k];
     }
     for (int k = 0; k < kPartials; ++k)
         sh[k * kSolveThreads + threadIdx.x] = k < 6 ? acc[k] : 0.0;
