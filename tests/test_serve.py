@@ -149,6 +149,11 @@ def test_native_plain_mode_serves_one_at_a_time(dev):
     reqs = serve.make_schedule(10, rate=1e6, seed=8, sizes=(128, 256), weights=(0.5, 0.5))
     stats = serve.NativeServer("plain").run(reqs)
     assert stats.images == 10 and stats.max_batch == 1 and stats.max_inflight == 1
+    # the loop's own timing record and the per-size split of the latencies
+    assert set(stats.loop) == {"max_yield_ms", "max_iter_ms", "yields_over_1ms"}
+    assert stats.loop["max_iter_ms"] >= 0.0 and stats.loop["yields_over_1ms"] >= 0
+    by = stats.summary()["by_size"]
+    assert sum(v["n"] for v in by.values()) == 10 and set(by) <= {"128", "256"}
     for r in reqs[:4]:
         ref = alone(r, dev)
         tol = TOL if r.order == "SURE" else 0.0
