@@ -53,9 +53,9 @@ OPS_PER_PAIR_IIR = 15
 # --no-cpu-baseline --no-rc --no-bf --no-nlm2d --no-3d --no-iir --no-fp16
 # --no-precision`; valid only while the pass kernels' sources (PASS_KERNEL_SOURCES)
 # hash to `sources_sha` (profiles/ has the capture's summary).
-TRAFFIC = {"sources_sha": "11ccc9ab695ad27c",
-           "bytes_per_launch": {"row_pass_sure/slide": 89504768, "col_pass_sure/block": 175620608,
-                                "col_pass_sure/slide": 92700416, "row_pass_sure/block": 264653056}}
+TRAFFIC = {"sources_sha": "52540b9a38cf68b2",
+           "bytes_per_launch": {"row_pass_sure/slide": 89521152, "col_pass_sure/block": 175208704,
+                                "col_pass_sure/slide": 92434176, "row_pass_sure/block": 264592128}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:

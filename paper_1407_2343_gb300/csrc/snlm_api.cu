@@ -326,7 +326,11 @@ int denoise_core(const void *img, int dtype, int H, int W, int pitch, int S, int
                                  &n_cr));
         {
             TraceScope ts(SNLM_K_SURE_SOLVE, st);
-            SNLM_TRY(launch_sure_solve(part_rc, n_rc, part_cr, n_cr, (double)sigma * sigma, winfo, wsolve, st));
+            // the reduction's ticket word sits in the info area's spare tail (info uses 10
+            // of its 32 doubles)
+            unsigned *ticket = reinterpret_cast<unsigned *>(winfo + 16);
+            SNLM_TRY(launch_sure_solve(part_rc, n_rc, part_cr, n_cr, (double)sigma * sigma, winfo, wsolve, ticket,
+                                       st));
         }
         {
             TraceScope ts(SNLM_K_COMBINE, st);

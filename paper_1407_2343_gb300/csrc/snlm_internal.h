@@ -183,10 +183,11 @@ constexpr int kTraceTma = 1 << 12;   // trace-kind flag: the launch used the TMA
 
 template <int K> cudaError_t launch_dist(const DistArgs &a, int dist_mode, cudaStream_t st);
 
-// scratch: 2 * kSolveScratchRecords * kPartials doubles
+// scratch: 2 * kSolveScratchRecords * kPartials doubles; ticket: one word of device
+// memory (zeroed on the stream by the launch)
 constexpr int kSolveScratchRecords = 128;
 cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
-                              double sigma2, double *info, double *scratch, cudaStream_t st);
+                              double sigma2, double *info, double *scratch, unsigned *ticket, cudaStream_t st);
 cudaError_t launch_combine(const float *frc, float *out_fcr, const double *info, long long n,
                            cudaStream_t st);
 cudaError_t launch_set_theta(double *info, double t1, double t2, cudaStream_t st);

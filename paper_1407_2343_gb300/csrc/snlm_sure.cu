@@ -32,14 +32,44 @@ __global__ void __launch_bounds__(kSolveThreads) sure_partial_kernel(const doubl
 // same minimiser (a linear change of variables; det/trace^2 is unchanged), but the
 // sums that fix the nearly singular direction (beta) are made of the small
 // differences d, so float32 per-pixel products keep them accurate.
-__global__ void __launch_bounds__(kSolveThreads) sure_solve_kernel(const double *part_rc, int n_rc,
-                                                                   const double *part_cr, int n_cr,
-                                                                   double sigma2, double *info)
+//
+// Both levels and the solve run in one launch: block b reduces slice b of each record
+// set into scratch (fixed order, as sure_partial_kernel), then takes a ticket; the
+// block that takes the last one (every slice is in scratch by then: each block
+// fences its writes before its ticket) reduces the slices in a fixed order and
+// solves. No block waits for another. The ticket word must be zero at launch.
+__global__ void __launch_bounds__(kSolveThreads) sure_reduce_solve_kernel(const double *part_rc, int n_rc,
+                                                                          int per_rc, const double *part_cr,
+                                                                          int n_cr, int per_cr, double *scratch,
+                                                                          unsigned *ticket, double sigma2,
+                                                                          double *info)
 {
     __shared__ double sh[kPartials * kSolveThreads];
+    __shared__ bool last;
+    double r[kPartials];
+    {
+        const int lo = blockIdx.x * per_rc, hi = min(n_rc, lo + per_rc);
+        reduce_records(part_rc + (long long)lo * kPartials, max(0, hi - lo), sh, r);
+        if (threadIdx.x < kPartials)
+            scratch[(long long)blockIdx.x * kPartials + threadIdx.x] = r[threadIdx.x];
+    }
+    {
+        const int lo = blockIdx.x * per_cr, hi = min(n_cr, lo + per_cr);
+        reduce_records(part_cr + (long long)lo * kPartials, max(0, hi - lo), sh, r);
+        if (threadIdx.x < kPartials)
+            scratch[(long long)(gridDim.x + blockIdx.x) * kPartials + threadIdx.x] = r[threadIdx.x];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
     double rc[kPartials], cr[kPartials];
-    reduce_records(part_rc, n_rc, sh, rc);
-    reduce_records(part_cr, n_cr, sh, cr);
+    reduce_records(scratch, gridDim.x, sh, rc);
+    reduce_records(scratch + (long long)gridDim.x * kPartials, gridDim.x, sh, cr);
     if (threadIdx.x == 0)
         sure_finish(rc, cr, sigma2, info);
 }
@@ -166,7 +196,7 @@ __global__ void set_theta_kernel(double *info, double t0, double t1)
 
 int preload_sure()
 {
-    const void *f[] = {(const void *)sure_partial_kernel, (const void *)sure_solve_kernel,
+    const void *f[] = {(const void *)sure_partial_kernel, (const void *)sure_reduce_solve_kernel,
                        (const void *)combine_kernel,      (const void *)combine_scalar_kernel,
                        (const void *)sure_sums_kernel,    (const void *)combine_theta_kernel,
                        (const void *)image_sums_kernel,   (const void *)set_theta_kernel};
@@ -177,16 +207,17 @@ int preload_sure()
 }
 
 cudaError_t launch_sure_solve(const double *part_rc, int n_rc, const double *part_cr, int n_cr,
-                              double sigma2, double *info, double *scratch, cudaStream_t st)
+                              double sigma2, double *info, double *scratch, unsigned *ticket, cudaStream_t st)
 {
-    // two fixed-order levels: kSolveBlocks slices per record set, then one block
+    // two fixed-order levels, kSolveBlocks slices per record set and then one block,
+    // in a single launch (the last block to finish does the second level)
     const int per_rc = (n_rc + kSolveBlocks - 1) / kSolveBlocks;
     const int per_cr = (n_cr + kSolveBlocks - 1) / kSolveBlocks;
-    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_rc, n_rc, per_rc, scratch);
-    sure_partial_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_cr, n_cr, per_cr,
-                                                                scratch + kSolveBlocks * kPartials);
-    sure_solve_kernel<<<1, kSolveThreads, 0, st>>>(scratch, kSolveBlocks, scratch + kSolveBlocks * kPartials,
-                                                   kSolveBlocks, sigma2, info);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess)
+        return e;
+    sure_reduce_solve_kernel<<<kSolveBlocks, kSolveThreads, 0, st>>>(part_rc, n_rc, per_rc, part_cr, n_cr, per_cr,
+                                                                     scratch, ticket, sigma2, info);
     return cudaGetLastError();
 }
 
