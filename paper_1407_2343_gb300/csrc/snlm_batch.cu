@@ -69,6 +69,7 @@ struct ClassInfo {
     int K = 0;
     int j0 = 0, nj = 0;       // job range (global indices, contiguous)
     int n_units = 0;
+    int u_off = 0;            // the class's first entry in the unit -> job table
     size_t smem = 0;          // dynamic shared memory of the class kernel
     int grid = 0;
 };
@@ -99,7 +100,8 @@ struct snlm_batch_plan {
     std::vector<BatchJob> jobs;
     std::vector<ClassInfo> classes;
     std::vector<Reloc> relocs;
-    size_t ws_bytes = 0, jobs_off = 0, done_off = 0, ctl_off = 0, scratch_off = 0;
+    std::vector<int> unit_job;    // job of every unit, class after class
+    size_t ws_bytes = 0, jobs_off = 0, done_off = 0, ctl_off = 0, scratch_off = 0, units_off = 0;
     snlm_batch_config cfg{};
     void *ws = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -372,10 +374,17 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
             return SNLM_ERR_ARG;
         P->jobs[P->cfg.fail_job].need0 += 1;   // never reached: host-side fault injection
     }
-    for (const ClassInfo &c : P->classes)
+    for (ClassInfo &c : P->classes) {
+        c.u_off = P->units;
         P->units += c.n_units;
+    }
+    P->unit_job.resize((size_t)P->units);
+    for (const ClassInfo &c : P->classes)
+        for (int q = c.j0; q < c.j0 + c.nj; ++q)
+            for (int u = 0; u < P->jobs[q].n_units; ++u)
+                P->unit_job[(size_t)c.u_off + P->jobs[q].unit0 + u] = q;
 
-    // workspace: control block | done counters | job table | scratch
+    // workspace: control block | done counters | job table | unit -> job table | scratch
     size_t o = 0;
     P->ctl_off = o;
     o += align_up(sizeof(BatchCtl), 256);
@@ -383,6 +392,8 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     o += align_up(P->jobs.size() * sizeof(int), 256);
     P->jobs_off = o;
     o += align_up(P->jobs.size() * sizeof(BatchJob), 256);
+    P->units_off = o;
+    o += align_up(P->unit_job.size() * sizeof(int), 256);
     P->scratch_off = o;
     P->ws_bytes = o + scratch_bytes;
     *plan_out = P.release();
@@ -437,6 +448,9 @@ int snlm_batch_plan_upload(snlm_batch_plan *P, void *workspace, size_t bytes, vo
     // returns, so the local table may go out of scope right after
     cudaError_t e = cudaMemcpyAsync(base + P->jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob),
                                     cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !P->unit_job.empty())
+        e = cudaMemcpyAsync(base + P->units_off, P->unit_job.data(), P->unit_job.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess)
         return status_of(e);
     // kernel attributes and persistent grid sizes (every CTA resident)
@@ -480,7 +494,8 @@ static int launch_raw(snlm_batch_plan *P, cudaStream_t st)
     for (int ci = 0; ci < (int)P->classes.size(); ++ci) {
         const ClassInfo &c = P->classes[ci];
         TraceScope ts(SNLM_K_BATCH, st);
-        batch_fn(c.K)<<<c.grid, kWarpsPerCta * 32, c.smem, st>>>(jobs, c.j0, c.nj, c.n_units, ci, ctl, done,
+        const int *unit_job = reinterpret_cast<const int *>(base + P->units_off) + c.u_off;
+        batch_fn(c.K)<<<c.grid, kWarpsPerCta * 32, c.smem, st>>>(jobs, unit_job, c.n_units, ci, ctl, done,
                                                                   limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess)

@@ -91,36 +91,35 @@ __device__ __forceinline__ void run_pass_unit(const BatchJob &j, int unit, float
     }
 }
 
-// One persistent CTA loop over the units of one K class.
+// One persistent CTA loop over the units of one K class. unit_job[u] is the job of
+// the class's unit u (a table built with the plan). Thread 0 claims the CTA's next
+// unit while the CTA works on the current one, so the claim's round trip to L2 is
+// hidden; units are still taken in increasing order per CTA, and every unit's
+// dependencies lie in earlier jobs, so the lowest unfinished unit is always one
+// that some CTA is working on. The job record is copied to shared memory only when
+// the job changes (consecutive units usually share it).
 template <int K>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
-batch_kernel(const BatchJob *__restrict__ jobs, int j0, int nj, int n_units, int cls, BatchCtl *ctl,
-             int *done, unsigned long long limit_ns)
+batch_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
+             BatchCtl *ctl, int *done, unsigned long long limit_ns)
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(16) BatchJob sj;
     __shared__ int s_unit, s_job, s_fail;
+    int next = 0, have = -1;                   // thread 0: claimed next unit; job held in sj
+    if (threadIdx.x == 0)
+        next = ld_acquire(&ctl->err) == 0 ? atomicAdd(&ctl->head[cls], 1) : n_units;
     for (;;) {
         if (threadIdx.x == 0) {
-            int u = n_units, jb = -1, fail = 0;
-            if (ld_acquire(&ctl->err) == 0) {
-                u = atomicAdd(&ctl->head[cls], 1);
-                if (u < n_units) {
-                    // job of unit u: the last job of the class with unit0 <= u
-                    int lo = j0, hi = j0 + nj - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (jobs[mid].unit0 <= u)
-                            lo = mid;
-                        else
-                            hi = mid - 1;
-                    }
-                    jb = lo;
-                    const BatchJob &J = jobs[jb];
-                    if ((J.dep0 >= 0 && !wait_count(done + J.dep0, J.need0, limit_ns)) ||
-                        (J.dep1 >= 0 && !wait_count(done + J.dep1, J.need1, limit_ns)))
-                        fail = 1;
-                }
+            int u = next, jb = -1, fail = 0;
+            if (u < n_units && ld_acquire(&ctl->err) != 0)
+                u = n_units;
+            if (u < n_units) {
+                jb = unit_job[u];
+                const BatchJob &J = jobs[jb];
+                if ((J.dep0 >= 0 && !wait_count(done + J.dep0, J.need0, limit_ns)) ||
+                    (J.dep1 >= 0 && !wait_count(done + J.dep1, J.need1, limit_ns)))
+                    fail = 1;
             }
             if (fail) {
                 atomicExch(&ctl->err_job, jb);
@@ -135,13 +134,16 @@ batch_kernel(const BatchJob *__restrict__ jobs, int j0, int nj, int n_units, int
         const int u = s_unit;
         if (u >= n_units || s_fail)
             return;
-        {
-            const int *src = reinterpret_cast<const int *>(jobs + s_job);
+        if (threadIdx.x == 0)
+            next = atomicAdd(&ctl->head[cls], 1);
+        if (s_job != have) {
+            have = s_job;
+            const int *src = reinterpret_cast<const int *>(jobs + have);
             int *dst = reinterpret_cast<int *>(&sj);
             for (int i = threadIdx.x; i < (int)(sizeof(BatchJob) / sizeof(int)); i += blockDim.x)
                 dst[i] = src[i];
+            __syncthreads();
         }
-        __syncthreads();
         const int unit = u - sj.unit0;
         if (sj.kind == kKindPass) {
             run_pass_unit<K>(sj, unit, smem);
@@ -164,7 +166,7 @@ batch_kernel(const BatchJob *__restrict__ jobs, int j0, int nj, int n_units, int
     }
 }
 
-using BatchFn = void (*)(const BatchJob *, int, int, int, int, BatchCtl *, int *, unsigned long long);
+using BatchFn = void (*)(const BatchJob *, const int *, int, int, BatchCtl *, int *, unsigned long long);
 
 // The class kernel of patch half-width K (defined in snlm_batch_k<K>.cu).
 template <int K>
