@@ -323,7 +323,8 @@ typedef struct {
 } snlm_request;
 
 typedef struct {
-    int ctas_per_sm;   /* persistent CTAs per SM; <= 0: as many as fit */
+    int ctas_per_sm;   /* cap on resident CTAs per SM (applied through each CTA's
+                          share of shared memory); <= 0: as many as fit */
     int queue_order;   /* 0: as given, 1: largest images first, 2: smallest first */
     int spin_limit_us; /* bound of one dependency wait; <= 0: 2 000 000 */
     int fail_job;      /* testing aid: >= 0 makes that job's first dependency
@@ -341,9 +342,10 @@ size_t snlm_batch_plan_workspace_bytes(const snlm_batch_plan *plan);
 /* Copies the job table into `workspace` (16-byte aligned, >= the bytes above) on
  * `stream` and binds the plan to it. */
 int snlm_batch_plan_upload(snlm_batch_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
-/* Queues one run of the whole batch on `stream` (counter reset + one persistent
- * kernel per K class); replays the captured graph if snlm_batch_plan_capture was
- * called. */
+/* Queues one run of the whole batch on `stream` (counter reset + one kernel per
+ * class: each pass variant and K, then the solve and combination jobs; one CTA per
+ * unit, each taking the next unit of its class's queue); replays the captured graph
+ * if snlm_batch_plan_capture was called. */
 int snlm_batch_plan_launch(snlm_batch_plan *plan, void *stream);
 /* Records one run into a CUDA graph (stream capture on `stream`, thread-local
  * mode) and instantiates it; later launches replay the graph. */
@@ -541,7 +543,7 @@ int snlm_device_error(void *stream);
  * be NULL) receives the number of kernels loaded, SNLM_KERNEL_COUNT when all were.
  * Returns SNLM_OK, or SNLM_ERR_CUDA if some kernel could not be loaded.
  */
-#define SNLM_KERNEL_COUNT 198
+#define SNLM_KERNEL_COUNT 234
 int snlm_preload(int *n_loaded);
 
 #ifdef __cplusplus

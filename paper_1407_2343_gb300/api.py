@@ -74,7 +74,7 @@ def snlm_version() -> int:
     return int(_lib.load().snlm_version())
 
 
-KERNEL_COUNT = 198   # SNLM_KERNEL_COUNT of include/snlm.h
+KERNEL_COUNT = 234   # SNLM_KERNEL_COUNT of include/snlm.h
 
 
 def snlm_preload() -> int:

@@ -1,15 +1,17 @@
-// Batched separable NLM: many independent images in persistent launches over a
-// work queue of CTA-sized units (declared in include/snlm.h, snlm_batch_*).
+// Batched separable NLM: many independent images in a few launches over a work
+// queue of CTA-sized units (declared in include/snlm.h, snlm_batch_*).
 //
 // Each image becomes jobs: one per 1-D pass of its order (Alg. 4: rows then
 // columns, columns then rows), and for SURE a solve job and combination jobs
 // (Eqs. (14), (19), (25)). A job is split into units (kWarpsPerCta lines x one
-// tile, exactly the units of the single-image kernels). Units are queued by
-// dependency level — every unit of level l comes before any unit of level l+1 — so
-// a unit only ever waits for units that were dequeued before it by CTAs that are
-// already running: with every CTA of the grid resident, the waits always end.
+// tile, exactly the units of the single-image kernels). Jobs are grouped into
+// classes, one kernel launch each (a pass variant and K, or the solve and
+// combination jobs), launched one after another; inside a class units are queued by
+// dependency level — every unit of level l comes before any unit of level l+1 — and
+// a CTA takes the next unit of the queue when it starts, so a unit only ever waits
+// for units taken before it by CTAs that are running or done: the waits always end.
 // They are bounded anyway (a time limit read from %globaltimer); a CTA that gives
-// up records it in the control block and stops taking work.
+// up records it in the control block, and the CTAs after it do no work.
 #include <algorithm>
 #include <cstddef>
 #include <memory>
@@ -19,68 +21,111 @@
 #include "snlm_batch_impl.cuh"
 
 namespace snlm {
+namespace batch {
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+batch_misc_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
+                  BatchCtl *ctl, int *done, unsigned long long limit_ns)
+{
+    extern __shared__ __align__(16) float smem[];
+    run_unit(jobs, unit_job, n_units, cls, ctl, done, limit_ns, smem, [](const BatchJob &j, int unit, float *sm) {
+        if (j.kind == kKindSolve) {
+            double rc[kPartials], cr[kPartials];
+            double *sh = reinterpret_cast<double *>(sm);
+            reduce_records(j.part_rc, j.n_rc, sh, rc);
+            reduce_records(j.part_cr, j.n_cr, sh, cr);
+            if (threadIdx.x == 0)
+                sure_finish(rc, cr, j.sigma2, j.info);
+        } else {
+            const long long lo = (long long)unit * kCombineChunk;
+            combine_range(j.frc, j.out, j.info, lo, min(j.n_px, lo + kCombineChunk));
+        }
+    });
+}
+
+}  // namespace batch
+
 namespace {
 
 using namespace snlm::batch;
 
-BatchFn batch_fn(int K)
+// The class kernel of (K, variant): variant = distance mode * 2 + SURE for the
+// passes, kVariantMisc for the solve and combination jobs.
+BatchFn batch_fn(int K, int variant)
 {
+    if (variant == kVariantMisc)
+        return batch_misc_kernel;
     switch (K) {
-    case 1: return batch_kernel_ptr<1>();
-    case 2: return batch_kernel_ptr<2>();
-    case 3: return batch_kernel_ptr<3>();
-    case 4: return batch_kernel_ptr<4>();
-    case 5: return batch_kernel_ptr<5>();
-    case 6: return batch_kernel_ptr<6>();
-    case 7: return batch_kernel_ptr<7>();
+    case 1: return batch_pass_kernel_ptr<1>(variant);
+    case 2: return batch_pass_kernel_ptr<2>(variant);
+    case 3: return batch_pass_kernel_ptr<3>(variant);
+    case 4: return batch_pass_kernel_ptr<4>(variant);
+    case 5: return batch_pass_kernel_ptr<5>(variant);
+    case 6: return batch_pass_kernel_ptr<6>(variant);
+    case 7: return batch_pass_kernel_ptr<7>(variant);
     default: return nullptr;
     }
 }
 
-// Shared-memory limit and occupancy of a class kernel, cached per (device, K, bytes):
-// the shared-memory attribute only ever grows, and a serving loop builds a plan
-// per step.
-cudaError_t class_occupancy(BatchFn fn, int dev, int K, size_t smem, int *occ)
+// Shared-memory limit and occupancy of a class kernel, cached per (device, kernel,
+// bytes): the shared-memory attribute only ever grows, and a serving loop builds a
+// plan per step.
+cudaError_t class_occupancy(BatchFn fn, int dev, size_t smem, int *occ)
 {
+    struct Entry {
+        int dev;
+        BatchFn fn;
+        size_t smem;
+        int occ;
+    };
     static std::mutex mu;
-    static std::vector<std::pair<long long, int>> cache;   // key -> occupancy
-    static std::vector<size_t> attr(64 * 8, 0);             // (dev, K) -> attribute set
-    const long long key = ((long long)dev << 40) | ((long long)K << 32) | (long long)smem;
+    static std::vector<Entry> cache;
+    static std::vector<Entry> attr;     // (dev, fn) -> the attribute set so far (in .smem)
     std::lock_guard<std::mutex> g(mu);
-    for (const auto &kv : cache)
-        if (kv.first == key) {
-            *occ = kv.second;
+    for (const Entry &c : cache)
+        if (c.dev == dev && c.fn == fn && c.smem == smem) {
+            *occ = c.occ;
             return cudaSuccess;
         }
-    const size_t slot = (size_t)(dev % 64) * 8 + (size_t)K;
-    if (attr[slot] < smem) {
+    Entry *slot = nullptr;
+    for (Entry &a : attr)
+        if (a.dev == dev && a.fn == fn)
+            slot = &a;
+    if (!slot) {
+        attr.push_back(Entry{dev, fn, 0, 0});
+        slot = &attr.back();
+    }
+    if (slot->smem < smem) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        attr[slot] = smem;
+        slot->smem = smem;
     }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kWarpsPerCta * 32, smem);
     if (e == cudaSuccess)
-        cache.push_back({key, *occ});
+        cache.push_back(Entry{dev, fn, smem, *occ});
     return e;
 }
 
 struct ClassInfo {
-    int K = 0;
+    int K = 0;                // 0 for the class of the solve and combination jobs
+    int variant = 0;
     int j0 = 0, nj = 0;       // job range (global indices, contiguous)
     int n_units = 0;
     int u_off = 0;            // the class's first entry in the unit -> job table
-    size_t smem = 0;          // dynamic shared memory of the class kernel
-    int grid = 0;
+    size_t smem = 0;          // dynamic shared memory the class kernel needs
+    size_t smem_launch = 0;   // and launches with (more when CTAs per SM are capped)
+    int grid = 0;             // one CTA per unit
 };
 
 }  // namespace
 
 int preload_batch()
 {
-    int n = 0;
+    int n = preload_kernel((const void *)batch_fn(0, kVariantMisc));
     for (int K = 1; K <= 7; ++K)
-        n += preload_kernel((const void *)batch_fn(K));
+        for (int v = 0; v < kVariants; ++v)
+            n += preload_kernel((const void *)batch_fn(K, v));
     return n;
 }
 
@@ -315,15 +360,25 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     }
     const size_t scratch_bytes = off;
 
-    // classes by K; inside a class, jobs by level, then by the queue policy
+    // Classes: one per (pass variant, K), then one for the solve and combination jobs;
+    // the class kernels run one after another on the stream in this order. A pass
+    // reading the image uses any variant, a pass reading a float intermediate the
+    // block-sum or Gaussian one, and the solve and combination come last, so every
+    // dependency lies in the same class (at a lower level) or in an earlier class.
+    // Inside a class, jobs by level, then by the queue policy.
     std::vector<int> rank(n);
     for (int k = 0; k < n; ++k)
         rank[order[k]] = k;
+    auto variant_of = [](const BatchJob &j) { return j.kind == kKindPass ? j.dm * 2 + j.sure : kVariantMisc; };
+    auto class_K = [&](const Proto &p) { return p.j.kind == kKindPass ? reqs[p.req].K : 0; };
     std::vector<int> idx(protos.size());
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
         const Proto &pa = protos[a], &pb = protos[b];
-        const int ka = reqs[pa.req].K, kb = reqs[pb.req].K;
+        const int va = variant_of(pa.j), vb = variant_of(pb.j);
+        if (va != vb)
+            return va < vb;
+        const int ka = class_K(pa), kb = class_K(pb);
         if (ka != kb)
             return ka < kb;
         if (pa.level != pb.level)
@@ -334,7 +389,7 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     for (size_t q = 0; q < idx.size(); ++q)
         new_index[idx[q]] = (int)q;
     P->jobs.resize(protos.size());
-    int cur_K = -1;
+    int cur_K = -1, cur_v = -1;
     for (size_t q = 0; q < idx.size(); ++q) {
         const Proto &pr = protos[idx[q]];
         BatchJob j = pr.j;
@@ -343,12 +398,17 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
         if (j.dep1 >= 0)
             j.dep1 = new_index[j.dep1];
         const int K = reqs[pr.req].K;
-        if (K != cur_K) {
+        const int v = variant_of(j), cK = class_K(pr);
+        if (cK != cur_K || v != cur_v) {
+            if ((int)P->classes.size() >= kMaxClasses)
+                return SNLM_ERR_UNSUPPORTED;
             ClassInfo ci;
-            ci.K = K;
+            ci.K = cK;
+            ci.variant = v;
             ci.j0 = (int)q;
             P->classes.push_back(ci);
-            cur_K = K;
+            cur_K = cK;
+            cur_v = v;
         }
         ClassInfo &ci = P->classes.back();
         j.unit0 = ci.n_units;
@@ -453,20 +513,39 @@ int snlm_batch_plan_upload(snlm_batch_plan *P, void *workspace, size_t bytes, vo
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess)
         return status_of(e);
-    // kernel attributes and persistent grid sizes (every CTA resident)
-    int dev = 0, sms = 0;
+    // kernel attributes, one CTA per unit; a cap on CTAs per SM is applied by giving
+    // each CTA that share of the SM's shared memory
+    int dev = 0, smem_sm = 0, reserved = 0, optin = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (ClassInfo &c : P->classes) {
-        BatchFn fn = batch_fn(c.K);
+        BatchFn fn = batch_fn(c.K, c.variant);
         if (!fn)
             return SNLM_ERR_UNSUPPORTED;
         int occ = 0;
-        e = class_occupancy(fn, dev, c.K, c.smem, &occ);
+        e = class_occupancy(fn, dev, c.smem, &occ);
         if (e != cudaSuccess || occ < 1)
             return e != cudaSuccess ? status_of(e) : SNLM_ERR_UNSUPPORTED;
-        const int per_sm = P->cfg.ctas_per_sm > 0 ? std::min(P->cfg.ctas_per_sm, occ) : occ;
-        c.grid = std::max(1, std::min(per_sm * sms, c.n_units));
+        c.smem_launch = c.smem;
+        if (P->cfg.ctas_per_sm > 0 && P->cfg.ctas_per_sm < occ) {
+            // the CTA's dynamic share: its part of the SM less the reserved and static
+            // shared memory, and at most what one CTA may have
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, fn);
+            if (e != cudaSuccess)
+                return status_of(e);
+            const long long st_b = (long long)fa.sharedSizeBytes;
+            long long share = std::min((long long)smem_sm / P->cfg.ctas_per_sm - reserved - st_b,
+                                       (long long)optin - st_b);
+            share = std::max(0LL, share) & ~127LL;
+            c.smem_launch = std::max(c.smem, (size_t)share);
+            e = class_occupancy(fn, dev, c.smem_launch, &occ);
+            if (e != cudaSuccess)
+                return status_of(e);
+        }
+        c.grid = std::max(1, c.n_units);
     }
     P->ws = workspace;
     if (P->exec) {
@@ -495,8 +574,8 @@ static int launch_raw(snlm_batch_plan *P, cudaStream_t st)
         const ClassInfo &c = P->classes[ci];
         TraceScope ts(SNLM_K_BATCH, st);
         const int *unit_job = reinterpret_cast<const int *>(base + P->units_off) + c.u_off;
-        batch_fn(c.K)<<<c.grid, kWarpsPerCta * 32, c.smem, st>>>(jobs, unit_job, c.n_units, ci, ctl, done,
-                                                                  limit_ns);
+        batch_fn(c.K, c.variant)<<<c.grid, kWarpsPerCta * 32, c.smem_launch, st>>>(jobs, unit_job, c.n_units, ci,
+                                                                                    ctl, done, limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess)
             return status_of(e);

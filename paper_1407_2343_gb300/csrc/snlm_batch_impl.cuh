@@ -1,7 +1,9 @@
 // Device side of the batched persistent launch (snlm_batch.cu): the job and
-// control records, the bounded dependency waits and the per-K class kernel. Each
-// class kernel is instantiated in a translation unit of its own (snlm_batch_k*.cu)
-// so that the library's build compiles them in parallel.
+// control records, the bounded dependency waits and the class kernels: one per
+// (K, pass variant) with the pass inlined as in the single-image kernel, and one for
+// the solve and combination jobs. The pass class kernels of each K are instantiated
+// in a translation unit of their own (snlm_batch_k*.cu) so that the library's build
+// compiles them in parallel.
 #pragma once
 
 #include "snlm_host.h"
@@ -14,7 +16,9 @@ namespace batch {
 
 constexpr int kKindPass = 0, kKindSolve = 1, kKindCombine = 2;
 constexpr int kCombineChunk = 4096;      // pixels per combination unit
-constexpr int kMaxClasses = 8;           // K = 1..7 (index K)
+constexpr int kVariants = 6;            // pass variants: distance mode x SURE
+constexpr int kVariantMisc = kVariants; // the class of the solve and combination jobs
+constexpr int kMaxClasses = 7 * kVariants + 1;
 
 struct BatchJob {
     PassArgs a;            // pass jobs
@@ -69,51 +73,27 @@ static __device__ bool wait_count(const int *ctr, int need, unsigned long long l
     return true;
 }
 
-// Each pass variant is its own (not inlined) function, so that its registers are
-// allocated for it alone rather than for the union of six inlined bodies.
-template <int K, int DM, bool SURE>
-__device__ __noinline__ void pass_unit_variant(const PassArgs &a, int unit, float *smem)
+// One unit of a class kernel. The grid has one CTA per unit of the class, and a CTA
+// takes its unit with an atomic on the class head when it starts, not from its
+// block index: units are thus started in claim order, a unit's dependencies lie in
+// earlier jobs (lower units of the class, or earlier classes, which ran to the end
+// before this launch), and every unit claimed before it belongs to a CTA that is
+// running or done, so the lowest unfinished unit always belongs to a running CTA and
+// every wait ends. unit_job[u] is the job of the class's unit u (a table built with
+// the plan). work(job, unit, smem) runs the unit; `job` points to the job table in
+// global memory, read-only for the launch, so the pass code reads its arguments
+// through the read-only path. (A persistent loop over the units held the tile's
+// loop-invariant values in registers across units and spilled 0.5-1 KB per thread.)
+template <typename Work>
+__device__ __forceinline__ void run_unit(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job,
+                                         int n_units, int cls, BatchCtl *ctl, int *done,
+                                         unsigned long long limit_ns, float *smem, Work work)
 {
-    process_tile<K, DM, SURE>(a, unit, smem);
-}
-
-template <int K>
-__device__ __forceinline__ void run_pass_unit(const BatchJob &j, int unit, float *smem)
-{
-    const int sel = j.dm * 2 + j.sure;
-    switch (sel) {
-    case DIST_SLIDE * 2 + 0: pass_unit_variant<K, DIST_SLIDE, false>(j.a, unit, smem); break;
-    case DIST_SLIDE * 2 + 1: pass_unit_variant<K, DIST_SLIDE, true>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 0: pass_unit_variant<K, DIST_BLOCK, false>(j.a, unit, smem); break;
-    case DIST_BLOCK * 2 + 1: pass_unit_variant<K, DIST_BLOCK, true>(j.a, unit, smem); break;
-    case DIST_FIR * 2 + 0: pass_unit_variant<K, DIST_FIR, false>(j.a, unit, smem); break;
-    default: pass_unit_variant<K, DIST_FIR, true>(j.a, unit, smem); break;
-    }
-}
-
-// One persistent CTA loop over the units of one K class. unit_job[u] is the job of
-// the class's unit u (a table built with the plan). Thread 0 claims the CTA's next
-// unit while the CTA works on the current one, so the claim's round trip to L2 is
-// hidden; units are still taken in increasing order per CTA, and every unit's
-// dependencies lie in earlier jobs, so the lowest unfinished unit is always one
-// that some CTA is working on. The job record is copied to shared memory only when
-// the job changes (consecutive units usually share it).
-template <int K>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
-batch_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
-             BatchCtl *ctl, int *done, unsigned long long limit_ns)
-{
-    extern __shared__ __align__(16) float smem[];
-    __shared__ __align__(16) BatchJob sj;
     __shared__ int s_unit, s_job, s_fail;
-    int next = 0, have = -1;                   // thread 0: claimed next unit; job held in sj
-    if (threadIdx.x == 0)
-        next = ld_acquire(&ctl->err) == 0 ? atomicAdd(&ctl->head[cls], 1) : n_units;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            int u = next, jb = -1, fail = 0;
-            if (u < n_units && ld_acquire(&ctl->err) != 0)
-                u = n_units;
+    if (threadIdx.x == 0) {
+        int u = n_units, jb = -1, fail = 0;
+        if (ld_acquire(&ctl->err) == 0) {
+            u = atomicAdd(&ctl->head[cls], 1);
             if (u < n_units) {
                 jb = unit_job[u];
                 const BatchJob &J = jobs[jb];
@@ -121,59 +101,68 @@ batch_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job
                     (J.dep1 >= 0 && !wait_count(done + J.dep1, J.need1, limit_ns)))
                     fail = 1;
             }
-            if (fail) {
-                atomicExch(&ctl->err_job, jb);
-                atomicExch(&ctl->err, 1);
-                __threadfence();
-            }
-            s_unit = u;
-            s_job = jb;
-            s_fail = fail;
         }
-        __syncthreads();
-        const int u = s_unit;
-        if (u >= n_units || s_fail)
-            return;
-        if (threadIdx.x == 0)
-            next = atomicAdd(&ctl->head[cls], 1);
-        if (s_job != have) {
-            have = s_job;
-            const int *src = reinterpret_cast<const int *>(jobs + have);
-            int *dst = reinterpret_cast<int *>(&sj);
-            for (int i = threadIdx.x; i < (int)(sizeof(BatchJob) / sizeof(int)); i += blockDim.x)
-                dst[i] = src[i];
-            __syncthreads();
-        }
-        const int unit = u - sj.unit0;
-        if (sj.kind == kKindPass) {
-            run_pass_unit<K>(sj, unit, smem);
-        } else if (sj.kind == kKindSolve) {
-            double rc[kPartials], cr[kPartials];
-            double *sh = reinterpret_cast<double *>(smem);
-            reduce_records(sj.part_rc, sj.n_rc, sh, rc);
-            reduce_records(sj.part_cr, sj.n_cr, sh, cr);
-            if (threadIdx.x == 0)
-                sure_finish(rc, cr, sj.sigma2, sj.info);
-        } else {
-            const long long lo = (long long)unit * kCombineChunk;
-            combine_range(sj.frc, sj.out, sj.info, lo, min(sj.n_px, lo + kCombineChunk));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (fail) {
+            atomicExch(&ctl->err_job, jb);
+            atomicExch(&ctl->err, 1);
             __threadfence();
-            atomicAdd(done + s_job, 1);
         }
+        s_unit = u;
+        s_job = jb;
+        s_fail = fail;
+    }
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= n_units || s_fail)
+        return;
+    const BatchJob *__restrict__ job = jobs + s_job;
+    work(*job, u - job->unit0, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(done + s_job, 1);
     }
 }
 
+// The class kernel of the pass variant (K, DM, SURE): the single-image kernel's tile
+// code inlined, with its occupancy.
+template <int K, int DM, bool SURE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<K, DM, SURE>())
+batch_pass_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
+                  BatchCtl *ctl, int *done, unsigned long long limit_ns)
+{
+    extern __shared__ __align__(16) float smem[];
+    run_unit(jobs, unit_job, n_units, cls, ctl, done, limit_ns, smem,
+             [](const BatchJob &j, int unit, float *sm) { process_tile<K, DM, SURE>(j.a, unit, sm); });
+}
+
+// The class kernel of the solve and combination jobs of SURE.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+batch_misc_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
+                  BatchCtl *ctl, int *done, unsigned long long limit_ns);
+
 using BatchFn = void (*)(const BatchJob *, const int *, int, int, BatchCtl *, int *, unsigned long long);
 
-// The class kernel of patch half-width K (defined in snlm_batch_k<K>.cu).
+// The pass class kernel of (K, variant), variant = distance mode * 2 + SURE
+// (defined in snlm_batch_k<K>.cu).
 template <int K>
-BatchFn batch_kernel_ptr();
+BatchFn batch_pass_kernel_ptr(int variant);
 
 }  // namespace batch
 }  // namespace snlm
 
-#define SNLM_INSTANTIATE_BATCH_K(KK) \
-    template <> snlm::batch::BatchFn snlm::batch::batch_kernel_ptr<KK>() { return snlm::batch::batch_kernel<KK>; }
+#define SNLM_INSTANTIATE_BATCH_K(KK)                                                                  \
+    template <>                                                                                       \
+    snlm::batch::BatchFn snlm::batch::batch_pass_kernel_ptr<KK>(int variant)                          \
+    {                                                                                                 \
+        using namespace snlm;                                                                         \
+        switch (variant) {                                                                            \
+        case DIST_SLIDE * 2 + 0: return batch_pass_kernel<KK, DIST_SLIDE, false>;                     \
+        case DIST_SLIDE * 2 + 1: return batch_pass_kernel<KK, DIST_SLIDE, true>;                      \
+        case DIST_BLOCK * 2 + 0: return batch_pass_kernel<KK, DIST_BLOCK, false>;                     \
+        case DIST_BLOCK * 2 + 1: return batch_pass_kernel<KK, DIST_BLOCK, true>;                      \
+        case DIST_FIR * 2 + 0: return batch_pass_kernel<KK, DIST_FIR, false>;                         \
+        case DIST_FIR * 2 + 1: return batch_pass_kernel<KK, DIST_FIR, true>;                          \
+        default: return nullptr;                                                                      \
+        }                                                                                             \
+    }

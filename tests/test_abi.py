@@ -92,12 +92,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 def test_kernel_count_constant_matches_the_binding():
     """SNLM_KERNEL_COUNT (what snlm_preload reports when every kernel loaded) is the
     binding's KERNEL_COUNT, and equals the kernels the preload lists name: 14 pass and
-    distance variants and 6 TMA pass variants for each K in 0..7, the batch kernels of
-    K 1..7, 3 recursive-profile modes, 8 SURE kernels, 8 bilateral radii, 8 2-D NLM
-    half-widths and 4 kernels of the 3-D extension."""
+    distance variants and 6 TMA pass variants for each K in 0..7, the batch class
+    kernels (6 pass variants for each K in 1..7, and one for the solve and
+    combination jobs), 3 recursive-profile modes, 8 SURE kernels, 8 bilateral radii,
+    8 2-D NLM half-widths and 4 kernels of the 3-D extension."""
     from paper_1407_2343_gb300 import api
 
     text = open(os.path.join(ROOT, "include", "snlm.h")).read()
     m = re.search(r"#define\s+SNLM_KERNEL_COUNT\s+(\d+)", text)
     assert m and int(m.group(1)) == api.KERNEL_COUNT
-    assert api.KERNEL_COUNT == 8 * (14 + 6) + 7 + 3 + 8 + 8 + 8 + 4
+    assert api.KERNEL_COUNT == 8 * (14 + 6) + (7 * 6 + 1) + 3 + 8 + 8 + 8 + 4

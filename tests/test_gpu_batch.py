@@ -64,6 +64,24 @@ MIXED = [dict(H=64, W=90, dtype="u8", sigma=20, S=5, K=2),
          dict(H=200, W=180, dtype="u8", sigma=35, S=12, K=5)]
 
 
+def expected_classes(specs):
+    """One class per (pass variant, K) and one for the solve and combination jobs:
+    a pass over the stored image uses the running sums (uint8, box), the block sums
+    (other storage, box) or the Gaussian taps; a pass over a float intermediate the
+    block sums or the Gaussian taps; SURE passes are variants of their own."""
+    keys = set()
+    for s in specs:
+        gauss = s.get("profile", "box") == "gauss"
+        sure = s.get("order", "RC") == "SURE"
+        img = "fir" if gauss else ("slide" if s["dtype"] == "u8" else "block")
+        f32 = "fir" if gauss else "block"
+        keys.add((img, sure, s["K"]))
+        keys.add((f32, sure, s["K"]))
+        if sure:
+            keys.add(("misc",))
+    return len(keys)
+
+
 def oracle_out(r):
     """Alg. 4 of the FP64 oracle on the request's stored samples."""
     import oracle
@@ -96,7 +114,7 @@ def test_batch_matches_per_image(dev):
     reqs = make_requests(dev, MIXED)
     b = Batch(reqs)
     info = b.info()
-    assert info["classes"] == 4 and info["jobs"] > len(reqs)
+    assert info["classes"] == expected_classes(MIXED) == 11 and info["jobs"] > len(reqs)
     b.run()
     torch.cuda.synchronize()
     assert b.status() == api.OK
