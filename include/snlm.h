@@ -299,15 +299,17 @@ int snlm_denoise_noalloc(const void *img, int dtype, int H, int W, int pitch, in
 
 /*
  * Batched denoising of many independent images (uneven sizes, per-image S, K, h,
- * profile, order) in persistent launches over a tile work queue.
+ * profile, order) in a few launches over a tile work queue.
  *
  * A plan turns the requests into jobs (one per 1-D pass of an image, plus the
  * SURE solve and combination) and jobs into CTA-sized units (4 lines x one tile).
- * Units are queued by dependency level (all first passes, then all second passes,
- * ...), and one persistent kernel per patch half-width K pops them with an atomic
- * counter; a unit whose job depends on unfinished jobs waits on per-job completion
- * counters. Every wait is bounded (snlm_batch_config.spin_limit_us); when a bound
- * is hit the kernel records it and stops, and snlm_batch_plan_status returns
+ * Jobs are grouped into classes (a pass variant and K, or the solve and combination
+ * jobs), one kernel launch each; inside a class, units are queued by dependency
+ * level (all first passes, then all second passes, ...), and each CTA of the
+ * launch takes the next unit with an atomic counter when it starts; a unit whose
+ * job depends on unfinished jobs waits on per-job completion counters. Every wait
+ * is bounded (snlm_batch_config.spin_limit_us); when a bound is hit the kernel
+ * records it, the CTAs after it do no work, and snlm_batch_plan_status returns
  * SNLM_ERR_TIMEOUT. Each image's result equals snlm_denoise's bit for bit for the
  * RC, CR and AVG orders (same per-unit code); for SURE the per-image sums are
  * reduced in a different fixed order, so theta may differ in the last bits.
@@ -389,7 +391,7 @@ typedef enum {
     SNLM_K_SET_THETA = 6,      /* writes the fixed weights of the RC / CR / AVG orders */
     SNLM_K_PATCH_DIST = 7,     /* patch distances of Eq. (3) */
     SNLM_K_LINE_PASS = 8,      /* snlm_nlm_1d pass over arbitrary strided lines */
-    SNLM_K_BATCH = 9,          /* one persistent batch kernel (one K class) */
+    SNLM_K_BATCH = 9,          /* one batch class kernel (a pass variant and K, or the solve and combination) */
     SNLM_K_BILATERAL = 10,     /* bilateral post-filter of Sec. III-B (Eq. (BF)) */
     SNLM_K_NLM_2D = 11,        /* the 2-D NLM of Eqs. (1)-(2) (comparison workload) */
     SNLM_K_LINE_PASS_3D = 12,  /* a 1-D pass of the separable 3-D extension */
@@ -428,7 +430,7 @@ int snlm_probe_peaks(double *rates, void *stream);
  * and one of `streams` streams free up. A request of at least solo_pixels pixels,
  * or a lone request on an idle GPU, runs alone through the per-image path; the
  * consecutive smaller requests at the front of the queue (at most max_batch) run
- * as one batch plan (the persistent launch of snlm_batch_plan_*). Each launch
+ * as one batch plan (snlm_batch_plan_*). Each launch
  * copies its inputs in, runs, and copies its results out on its own stream, so
  * launches overlap on the device; half of the streams (at least one) have the
  * device's highest priority and carry the launches of requests below solo_pixels,

@@ -2,10 +2,11 @@
 
 `Batch` wraps a native batch plan (include/snlm.h, snlm_batch_*): the images'
 1-D passes (and the SURE solve/combination) are split into CTA-sized units queued
-by dependency level and run by one persistent kernel per patch half-width K; the
-whole run can be captured in a CUDA graph and replayed.
+by dependency level and run by one kernel per class (a pass variant and K, or the
+solve and combination), one CTA per unit; the whole run can be captured in a CUDA
+graph and replayed.
 
-`autotune` picks the launch parameters of a batch — persistent CTAs per SM and
+`autotune` picks the launch parameters of a batch — a cap on CTAs per SM and
 the queue order (as given, largest first, smallest first) — by timing graph
 replays of the batch itself, and caches the choice per GPU and batch signature.
 """

@@ -9,7 +9,7 @@
 //     as its device footprint fits in the server's slab: a request of at least
 //     solo_pixels pixels (or a lone request on an idle GPU) runs alone through the
 //     per-image path, otherwise the consecutive small requests at the front become
-//     one batch plan (the persistent launch over their tile units). The launch
+//     one batch plan (the launch over their tile units). The launch
 //     copies its inputs in, runs, and copies its results out to the callers' host
 //     buffers, all on its stream, then records an event;
 //  3. launches whose event has completed are retired: completion time, status,
