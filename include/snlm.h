@@ -303,14 +303,13 @@ int snlm_denoise_noalloc(const void *img, int dtype, int H, int W, int pitch, in
  *
  * A plan turns the requests into jobs (one per 1-D pass of an image, plus the
  * SURE solve and combination) and jobs into CTA-sized units (4 lines x one tile).
- * Jobs are grouped into classes (a pass variant and K, or the solve and combination
- * jobs), one kernel launch each; inside a class, units are queued by dependency
- * level (all first passes, then all second passes, ...), and each CTA of the
- * launch takes the next unit with an atomic counter when it starts; a unit whose
- * job depends on unfinished jobs waits on per-job completion counters. Every wait
- * is bounded (snlm_batch_config.spin_limit_us); when a bound is hit the kernel
- * records it, the CTAs after it do no work, and snlm_batch_plan_status returns
- * SNLM_ERR_TIMEOUT. Each image's result equals snlm_denoise's bit for bit for the
+ * Jobs are grouped into classes by dependency level (all first passes, then all
+ * second passes, ...) and kernel (a pass variant and K, or the solve or the
+ * combination), one launch each with one CTA per unit, run in level order, so a
+ * unit's dependencies are complete when it starts. Each CTA still checks them on
+ * per-job completion counters with a bounded wait (snlm_batch_config.spin_limit_us);
+ * when a bound is hit (only an injected fault does that) the kernel records it, the
+ * CTAs after it do no work, and snlm_batch_plan_status returns SNLM_ERR_TIMEOUT. Each image's result equals snlm_denoise's bit for bit for the
  * RC, CR and AVG orders (same per-unit code); for SURE the per-image sums are
  * reduced in a different fixed order, so theta may differ in the last bits.
  */
@@ -330,7 +329,10 @@ typedef struct {
     int queue_order;   /* 0: as given, 1: largest images first, 2: smallest first */
     int spin_limit_us; /* bound of one dependency wait; <= 0: 2 000 000 */
     int fail_job;      /* testing aid: >= 0 makes that job's first dependency
-                          unsatisfiable (host-side fault injection); -1 normally */
+                          unsatisfiable (host-side fault injection); -1 normally.
+                          Jobs are numbered in the plan's order (by dependency
+                          level); the last job always has a dependency, a job
+                          without one gives SNLM_ERR_ARG */
 } snlm_batch_config;
 
 typedef struct snlm_batch_plan snlm_batch_plan;
@@ -345,8 +347,7 @@ size_t snlm_batch_plan_workspace_bytes(const snlm_batch_plan *plan);
  * `stream` and binds the plan to it. */
 int snlm_batch_plan_upload(snlm_batch_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
 /* Queues one run of the whole batch on `stream` (counter reset + one kernel per
- * class: each pass variant and K, then the solve and combination jobs; one CTA per
- * unit, each taking the next unit of its class's queue); replays the captured graph
+ * class, in dependency-level order, one CTA per unit); replays the captured graph
  * if snlm_batch_plan_capture was called. */
 int snlm_batch_plan_launch(snlm_batch_plan *plan, void *stream);
 /* Records one run into a CUDA graph (stream capture on `stream`, thread-local

@@ -5,13 +5,14 @@
 // columns, columns then rows), and for SURE a solve job and combination jobs
 // (Eqs. (14), (19), (25)). A job is split into units (kWarpsPerCta lines x one
 // tile, exactly the units of the single-image kernels). Jobs are grouped into
-// classes, one kernel launch each (a pass variant and K, or the solve and
-// combination jobs), launched one after another; inside a class units are queued by
-// dependency level — every unit of level l comes before any unit of level l+1 — and
-// a CTA takes the next unit of the queue when it starts, so a unit only ever waits
-// for units taken before it by CTAs that are running or done: the waits always end.
-// They are bounded anyway (a time limit read from %globaltimer); a CTA that gives
-// up records it in the control block, and the CTAs after it do no work.
+// classes by dependency level (a job depends only on jobs of lower levels), then by
+// kernel (a pass variant and K, or the solve and combination jobs); each class is
+// one launch with one CTA per unit, and the classes run one after another on the
+// stream in level order, so every dependency of a unit is complete when its CTA
+// starts. The CTAs still check their dependencies' completion counters with a
+// bounded wait (a time limit read from %globaltimer), which only an injected fault
+// runs out; a CTA that gives up records it in the control block, and the CTAs after
+// it do no work.
 #include <algorithm>
 #include <cstddef>
 #include <memory>
@@ -24,11 +25,11 @@ namespace snlm {
 namespace batch {
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-batch_misc_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
-                  BatchCtl *ctl, int *done, unsigned long long limit_ns)
+batch_misc_kernel(const BatchJob *__restrict__ jobs, const UnitRec *__restrict__ recs, BatchCtl *ctl, int *done,
+                  unsigned long long limit_ns)
 {
     extern __shared__ __align__(16) float smem[];
-    run_unit(jobs, unit_job, n_units, cls, ctl, done, limit_ns, smem, [](const BatchJob &j, int unit, float *sm) {
+    run_unit(jobs, recs, ctl, done, limit_ns, smem, [](const BatchJob &j, int unit, float *sm) {
         if (j.kind == kKindSolve) {
             double rc[kPartials], cr[kPartials];
             double *sh = reinterpret_cast<double *>(sm);
@@ -112,7 +113,7 @@ struct ClassInfo {
     int variant = 0;
     int j0 = 0, nj = 0;       // job range (global indices, contiguous)
     int n_units = 0;
-    int u_off = 0;            // the class's first entry in the unit -> job table
+    int u_off = 0;            // the class's first entry in the unit records
     size_t smem = 0;          // dynamic shared memory the class kernel needs
     size_t smem_launch = 0;   // and launches with (more when CTAs per SM are capped)
     int grid = 0;             // one CTA per unit
@@ -145,7 +146,7 @@ struct snlm_batch_plan {
     std::vector<BatchJob> jobs;
     std::vector<ClassInfo> classes;
     std::vector<Reloc> relocs;
-    std::vector<int> unit_job;    // job of every unit, class after class
+    std::vector<UnitRec> unit_recs;   // every unit's record, class after class
     size_t ws_bytes = 0, jobs_off = 0, done_off = 0, ctl_off = 0, scratch_off = 0, units_off = 0;
     snlm_batch_config cfg{};
     void *ws = nullptr;
@@ -360,12 +361,11 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     }
     const size_t scratch_bytes = off;
 
-    // Classes: one per (pass variant, K), then one for the solve and combination jobs;
-    // the class kernels run one after another on the stream in this order. A pass
-    // reading the image uses any variant, a pass reading a float intermediate the
-    // block-sum or Gaussian one, and the solve and combination come last, so every
-    // dependency lies in the same class (at a lower level) or in an earlier class.
-    // Inside a class, jobs by level, then by the queue policy.
+    // Classes: one per (dependency level, pass variant, K), the solve and the
+    // combination jobs in classes of their own levels; the class kernels run one after
+    // another on the stream in this order, so every job a class depends on lies in an
+    // earlier class, complete when the class starts. Inside a class, jobs follow the
+    // queue policy.
     std::vector<int> rank(n);
     for (int k = 0; k < n; ++k)
         rank[order[k]] = k;
@@ -375,21 +375,21 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
         const Proto &pa = protos[a], &pb = protos[b];
+        if (pa.level != pb.level)
+            return pa.level < pb.level;
         const int va = variant_of(pa.j), vb = variant_of(pb.j);
         if (va != vb)
             return va < vb;
         const int ka = class_K(pa), kb = class_K(pb);
         if (ka != kb)
             return ka < kb;
-        if (pa.level != pb.level)
-            return pa.level < pb.level;
         return rank[pa.req] < rank[pb.req];
     });
     std::vector<int> new_index(protos.size());
     for (size_t q = 0; q < idx.size(); ++q)
         new_index[idx[q]] = (int)q;
     P->jobs.resize(protos.size());
-    int cur_K = -1, cur_v = -1;
+    int cur_K = -1, cur_v = -1, cur_l = -1;
     for (size_t q = 0; q < idx.size(); ++q) {
         const Proto &pr = protos[idx[q]];
         BatchJob j = pr.j;
@@ -399,9 +399,7 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
             j.dep1 = new_index[j.dep1];
         const int K = reqs[pr.req].K;
         const int v = variant_of(j), cK = class_K(pr);
-        if (cK != cur_K || v != cur_v) {
-            if ((int)P->classes.size() >= kMaxClasses)
-                return SNLM_ERR_UNSUPPORTED;
+        if (cK != cur_K || v != cur_v || pr.level != cur_l) {
             ClassInfo ci;
             ci.K = cK;
             ci.variant = v;
@@ -409,6 +407,7 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
             P->classes.push_back(ci);
             cur_K = cK;
             cur_v = v;
+            cur_l = pr.level;
         }
         ClassInfo &ci = P->classes.back();
         j.unit0 = ci.n_units;
@@ -438,13 +437,15 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
         c.u_off = P->units;
         P->units += c.n_units;
     }
-    P->unit_job.resize((size_t)P->units);
+    P->unit_recs.resize((size_t)P->units);
     for (const ClassInfo &c : P->classes)
-        for (int q = c.j0; q < c.j0 + c.nj; ++q)
-            for (int u = 0; u < P->jobs[q].n_units; ++u)
-                P->unit_job[(size_t)c.u_off + P->jobs[q].unit0 + u] = q;
+        for (int q = c.j0; q < c.j0 + c.nj; ++q) {
+            const BatchJob &J = P->jobs[q];
+            for (int u = 0; u < J.n_units; ++u)
+                P->unit_recs[(size_t)c.u_off + J.unit0 + u] = UnitRec{q, u, J.dep0, J.need0, J.dep1, J.need1, 0, 0};
+        }
 
-    // workspace: control block | done counters | job table | unit -> job table | scratch
+    // workspace: control block | done counters | job table | unit records | scratch
     size_t o = 0;
     P->ctl_off = o;
     o += align_up(sizeof(BatchCtl), 256);
@@ -453,7 +454,7 @@ int snlm_batch_plan_create(const snlm_request *reqs, int n, const snlm_batch_con
     P->jobs_off = o;
     o += align_up(P->jobs.size() * sizeof(BatchJob), 256);
     P->units_off = o;
-    o += align_up(P->unit_job.size() * sizeof(int), 256);
+    o += align_up(P->unit_recs.size() * sizeof(UnitRec), 256);
     P->scratch_off = o;
     P->ws_bytes = o + scratch_bytes;
     *plan_out = P.release();
@@ -508,8 +509,8 @@ int snlm_batch_plan_upload(snlm_batch_plan *P, void *workspace, size_t bytes, vo
     // returns, so the local table may go out of scope right after
     cudaError_t e = cudaMemcpyAsync(base + P->jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !P->unit_job.empty())
-        e = cudaMemcpyAsync(base + P->units_off, P->unit_job.data(), P->unit_job.size() * sizeof(int),
+    if (e == cudaSuccess && !P->unit_recs.empty())
+        e = cudaMemcpyAsync(base + P->units_off, P->unit_recs.data(), P->unit_recs.size() * sizeof(UnitRec),
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess)
         return status_of(e);
@@ -572,10 +573,11 @@ static int launch_raw(snlm_batch_plan *P, cudaStream_t st)
         (unsigned long long)(P->cfg.spin_limit_us > 0 ? P->cfg.spin_limit_us : 2000000) * 1000ULL;
     for (int ci = 0; ci < (int)P->classes.size(); ++ci) {
         const ClassInfo &c = P->classes[ci];
+        if (c.n_units < 1)
+            continue;
         TraceScope ts(SNLM_K_BATCH, st);
-        const int *unit_job = reinterpret_cast<const int *>(base + P->units_off) + c.u_off;
-        batch_fn(c.K, c.variant)<<<c.grid, kWarpsPerCta * 32, c.smem_launch, st>>>(jobs, unit_job, c.n_units, ci,
-                                                                                    ctl, done, limit_ns);
+        const UnitRec *recs = reinterpret_cast<const UnitRec *>(base + P->units_off) + c.u_off;
+        batch_fn(c.K, c.variant)<<<c.grid, kWarpsPerCta * 32, c.smem_launch, st>>>(jobs, recs, ctl, done, limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess)
             return status_of(e);

@@ -18,7 +18,6 @@ constexpr int kKindPass = 0, kKindSolve = 1, kKindCombine = 2;
 constexpr int kCombineChunk = 4096;      // pixels per combination unit
 constexpr int kVariants = 6;            // pass variants: distance mode x SURE
 constexpr int kVariantMisc = kVariants; // the class of the solve and combination jobs
-constexpr int kMaxClasses = 7 * kVariants + 1;
 
 struct BatchJob {
     PassArgs a;            // pass jobs
@@ -39,10 +38,18 @@ struct BatchJob {
 };
 
 struct BatchCtl {
-    int head[kMaxClasses];  // next unit of each class
     int err;                // a bounded wait gave up
     int err_job;
     int pad[6];
+};
+
+// What a CTA needs to start its unit, in one 32-byte record per unit (built with the
+// plan): the job, the unit's index inside the job, and the job's dependencies with
+// the completion counts they must reach.
+struct __align__(16) UnitRec {
+    int job, unit;
+    int dep0, need0, dep1, need1;
+    int pad0, pad1;
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -73,75 +80,66 @@ static __device__ bool wait_count(const int *ctr, int need, unsigned long long l
     return true;
 }
 
-// One unit of a class kernel. The grid has one CTA per unit of the class, and a CTA
-// takes its unit with an atomic on the class head when it starts, not from its
-// block index: units are thus started in claim order, a unit's dependencies lie in
-// earlier jobs (lower units of the class, or earlier classes, which ran to the end
-// before this launch), and every unit claimed before it belongs to a CTA that is
-// running or done, so the lowest unfinished unit always belongs to a running CTA and
-// every wait ends. unit_job[u] is the job of the class's unit u (a table built with
-// the plan). work(job, unit, smem) runs the unit; `job` points to the job table in
-// global memory, read-only for the launch, so the pass code reads its arguments
-// through the read-only path. (A persistent loop over the units held the tile's
-// loop-invariant values in registers across units and spilled 0.5-1 KB per thread.)
+// One unit of a class kernel: the grid has one CTA per unit of the class, CTA b
+// runs unit b. A class holds jobs of one dependency level, so every job a unit
+// depends on belongs to an earlier class, which the stream ran to the end before
+// this launch: the dependencies are complete when the CTA starts. The CTA still
+// checks the per-job completion counters (a bounded wait, which only an injected
+// fault can make run out), and releases its own unit by a counter increment that
+// later launches read. work(job, unit, smem) runs the unit; `job` points to the job
+// table in global memory, read-only for the launch, so the pass code reads its
+// arguments through the read-only path. (A persistent loop over the units held the
+// tile's loop-invariant values in registers across units and spilled 0.5-1 KB per
+// thread; taking units with an atomic claim put an L2 round trip before every
+// unit's work.)
 template <typename Work>
-__device__ __forceinline__ void run_unit(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job,
-                                         int n_units, int cls, BatchCtl *ctl, int *done,
-                                         unsigned long long limit_ns, float *smem, Work work)
+__device__ __forceinline__ void run_unit(const BatchJob *__restrict__ jobs, const UnitRec *__restrict__ recs,
+                                         BatchCtl *ctl, int *done, unsigned long long limit_ns, float *smem,
+                                         Work work)
 {
-    __shared__ int s_unit, s_job, s_fail;
+    __shared__ int s_job, s_unit, s_fail;
     if (threadIdx.x == 0) {
-        int u = n_units, jb = -1, fail = 0;
-        if (ld_acquire(&ctl->err) == 0) {
-            u = atomicAdd(&ctl->head[cls], 1);
-            if (u < n_units) {
-                jb = unit_job[u];
-                const BatchJob &J = jobs[jb];
-                if ((J.dep0 >= 0 && !wait_count(done + J.dep0, J.need0, limit_ns)) ||
-                    (J.dep1 >= 0 && !wait_count(done + J.dep1, J.need1, limit_ns)))
-                    fail = 1;
-            }
-        }
-        if (fail) {
-            atomicExch(&ctl->err_job, jb);
+        const UnitRec r = recs[blockIdx.x];
+        int fail = ld_acquire(&ctl->err) != 0 ? 2 : 0;
+        if (fail == 0 && ((r.dep0 >= 0 && !wait_count(done + r.dep0, r.need0, limit_ns)) ||
+                          (r.dep1 >= 0 && !wait_count(done + r.dep1, r.need1, limit_ns)))) {
+            fail = 1;
+            atomicExch(&ctl->err_job, r.job);
             atomicExch(&ctl->err, 1);
             __threadfence();
         }
-        s_unit = u;
-        s_job = jb;
+        s_job = r.job;
+        s_unit = r.unit;
         s_fail = fail;
     }
     __syncthreads();
-    const int u = s_unit;
-    if (u >= n_units || s_fail)
+    if (s_fail)
         return;
-    const BatchJob *__restrict__ job = jobs + s_job;
-    work(*job, u - job->unit0, smem);
+    const int jb = s_job;
+    work(jobs[jb], s_unit, smem);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(done + s_job, 1);
-    }
+    if (threadIdx.x == 0)
+        atomicAdd(done + jb, 1);
 }
 
 // The class kernel of the pass variant (K, DM, SURE): the single-image kernel's tile
 // code inlined, with its occupancy.
 template <int K, int DM, bool SURE>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, pass_min_ctas<K, DM, SURE>())
-batch_pass_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
-                  BatchCtl *ctl, int *done, unsigned long long limit_ns)
+batch_pass_kernel(const BatchJob *__restrict__ jobs, const UnitRec *__restrict__ recs, BatchCtl *ctl, int *done,
+                  unsigned long long limit_ns)
 {
     extern __shared__ __align__(16) float smem[];
-    run_unit(jobs, unit_job, n_units, cls, ctl, done, limit_ns, smem,
+    run_unit(jobs, recs, ctl, done, limit_ns, smem,
              [](const BatchJob &j, int unit, float *sm) { process_tile<K, DM, SURE>(j.a, unit, sm); });
 }
 
 // The class kernel of the solve and combination jobs of SURE.
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-batch_misc_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ unit_job, int n_units, int cls,
-                  BatchCtl *ctl, int *done, unsigned long long limit_ns);
+batch_misc_kernel(const BatchJob *__restrict__ jobs, const UnitRec *__restrict__ recs, BatchCtl *ctl, int *done,
+                  unsigned long long limit_ns);
 
-using BatchFn = void (*)(const BatchJob *, const int *, int, int, BatchCtl *, int *, unsigned long long);
+using BatchFn = void (*)(const BatchJob *, const UnitRec *, BatchCtl *, int *, unsigned long long);
 
 // The pass class kernel of (K, variant), variant = distance mode * 2 + SURE
 // (defined in snlm_batch_k<K>.cu).

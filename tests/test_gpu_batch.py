@@ -65,20 +65,28 @@ MIXED = [dict(H=64, W=90, dtype="u8", sigma=20, S=5, K=2),
 
 
 def expected_classes(specs):
-    """One class per (pass variant, K) and one for the solve and combination jobs:
-    a pass over the stored image uses the running sums (uint8, box), the block sums
-    (other storage, box) or the Gaussian taps; a pass over a float intermediate the
-    block sums or the Gaussian taps; SURE passes are variants of their own."""
+    """One class per (dependency level, pass variant, K), and the solve and the
+    combination jobs of SURE in classes of their own levels. A pass over the stored
+    image uses the running sums (uint8, box), the block sums (other storage, box) or
+    the Gaussian taps; a pass over a float intermediate the block sums or the
+    Gaussian taps; SURE passes are variants of their own. Levels: the passes over
+    the image 0, the pass over the first intermediate 1, the last pass of AVG and
+    SURE (which also reads the other order's result) 2, the solve 3, the combination
+    4."""
     keys = set()
     for s in specs:
         gauss = s.get("profile", "box") == "gauss"
-        sure = s.get("order", "RC") == "SURE"
+        order = s.get("order", "RC")
+        sure = order == "SURE"
         img = "fir" if gauss else ("slide" if s["dtype"] == "u8" else "block")
         f32 = "fir" if gauss else "block"
-        keys.add((img, sure, s["K"]))
-        keys.add((f32, sure, s["K"]))
+        keys.add((0, img, sure, s["K"]))
+        keys.add((2 if order in ("AVG", "SURE") else 1, f32, sure, s["K"]))
+        if order in ("AVG", "SURE"):
+            keys.add((1, f32, sure, s["K"]))
         if sure:
-            keys.add(("misc",))
+            keys.add((3, "solve"))
+            keys.add((4, "combine"))
     return len(keys)
 
 
@@ -114,7 +122,7 @@ def test_batch_matches_per_image(dev):
     reqs = make_requests(dev, MIXED)
     b = Batch(reqs)
     info = b.info()
-    assert info["classes"] == expected_classes(MIXED) == 11 and info["jobs"] > len(reqs)
+    assert info["classes"] == expected_classes(MIXED) and info["jobs"] > len(reqs)
     b.run()
     torch.cuda.synchronize()
     assert b.status() == api.OK
@@ -187,7 +195,11 @@ def test_batch_bounded_wait_reports_timeout(dev):
     from paper_1407_2343_gb300.batch import Batch
 
     reqs = make_requests(dev, MIXED[:3])
-    b = Batch(reqs, spin_limit_us=20000, fail_job=3)
+    # the plan's last job (the highest dependency level) has a dependency to break
+    probe = Batch(reqs)
+    last = probe.info()["jobs"] - 1
+    probe.close()
+    b = Batch(reqs, spin_limit_us=20000, fail_job=last)
     word = torch.full((1,), -7, dtype=torch.int32).pin_memory()
     st = torch.cuda.current_stream()
     b.run(st)
